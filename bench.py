@@ -1,0 +1,395 @@
+"""Throughput of per-pixel sparse recovery of a 2.5x compressed hyperspectral cube.
+
+One step = the whole hot path over one cube: measurement Y = X A^T + E (Eq. 1) and
+recovery of every pixel with each of the paper's five algorithms (FISTA, ADMM, gOMP,
+BIHT, CoSaMP; Section II-A), all through the C ABI of libcs_hsi.so.
+
+Workload: 512 x 512 pixels, N = 200 bands, M = 80 measurements (2.5x), Gaussian Phi,
+DCT-II Psi, power-law spectra |x_k| = k^-1.5 with random signs, N(0, 1e-3) noise;
+FISTA 300 iterations (lambda = 1e-3), ADMM 300 iterations (rho = 1, lambda = 1e-3),
+gOMP kappa = 20, G = 4; BIHT kappa = 20, mu = 0.1; CoSaMP kappa = 20; eps = 1e-8.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints one JSON line.  value = recovered spectra per second over the whole job
+(pixels x algorithms per step / step time).  The FP64 oracle (CPU) is timed on a
+bounded pixel sample on the host cores and its outputs on that sample give the
+accuracy of the GPU results (relative L2).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+M, N, SIDE = 80, 200, 512
+P = SIDE * SIDE
+LAM, ITERS, RHO, KAPPA, G, MU, EPS = 1e-3, 300, 1.0, 20, 4, 0.1, 1e-8
+NOISE_VAR, SEED = 1e-3, 1
+ALGOS = ["fista", "admm", "gomp", "biht", "cosamp"]
+METRIC = "recovered spectra/s at rel-L2<=1e-3 vs FP64 oracle, mixed vs FP32; % roofline"
+UNIT = "spectra/s"
+SM_COUNT, SM_MAX_MHZ = 152, 2070.0
+# Plain-ALU peaks derived from unit counts x clock (see the design notes):
+# FP32: 128 FMA lanes per SM; FP64: 1.25 TFLOP/s for the chip at the maximum clock.
+FP32_PEAK_TFLOPS = SM_COUNT * 128 * 2 * SM_MAX_MHZ * 1e6 / 1e12
+FP64_PEAK_TFLOPS = 1.25
+KERNEL_FILES = {"fista": "convex_f32.cu", "admm": "convex_f32.cu", "measure": "convex_f32.cu",
+                "gomp": "greedy.cu", "biht": "greedy.cu", "cosamp": "greedy.cu"}
+
+
+def config(extra=None):
+    c = {"workload": f"cube {SIDE}x{SIDE} x N={N}, M={M}; power-law spectra + N(0,1e-3) noise; "
+                     f"measure + FISTA({ITERS}) + ADMM({ITERS}) + gOMP(k={KAPPA},G={G}) + "
+                     f"BIHT(k={KAPPA}) + CoSaMP(k={KAPPA})",
+         "pixels": P, "bands": N, "measurements": M, "algorithms": ALGOS,
+         "spectra_per_step": P * len(ALGOS), "precision": "fp32",
+         "l2": "flushed between timed steps (256 MiB write)"}
+    if extra:
+        c.update(extra)
+    return c
+
+
+# ----------------------------------------------------------------------------- oracle leg
+def oracle_sample(n_pix, threads, X_true, E, Phi):
+    """Runs the FP64 oracle on the first n_pix pixels of the cube; returns outputs and time."""
+    import oracle as orc
+    A = orc.dictionary(Phi)
+    L = orc.lipschitz(A)
+    Y = orc.measure(A, X_true[:n_pix], E[:n_pix]).astype(np.float32)
+    out, t0 = {}, time.perf_counter()
+    out["fista"] = orc.fista(A, Y, L, LAM, EPS, ITERS, threads=threads)[0]
+    out["admm"] = orc.admm(A, Y, RHO, LAM, EPS, ITERS, threads=threads)[0]
+    out["gomp"] = orc.gomp(A, Y, KAPPA, G, EPS, threads=threads)
+    out["biht"] = orc.biht(A, Y, KAPPA, MU, EPS, 100, threads=threads)
+    out["cosamp"] = orc.cosamp(A, Y, KAPPA, EPS, 100, threads=threads)
+    secs = time.perf_counter() - t0
+    return out, secs
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def sample_inputs(n_pix):
+    from paper_2401_14762_gb300 import synthetic as sy
+    Phi = sy.gaussian_phi(M, N, SEED)
+    X = sy.powerlaw_coeffs(n_pix, N, SEED)
+    E = sy.noise(n_pix, M, NOISE_VAR, SEED)
+    return Phi, X, E
+
+
+def run_reference(args):
+    """The oracle as it stands, on the host cores, each step a bounded pixel sample."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    n_pix = 256
+    cores = host_cores()
+    Phi, X, E = sample_inputs(n_pix)
+    for _ in range(args.warmup):
+        oracle_sample(32, cores, X, E, Phi)
+    times = []
+    for _ in range(args.steps):
+        _, secs = oracle_sample(n_pix, cores, X, E, Phi)
+        times.append(secs)
+    t = sum(times) / len(times)
+    value = n_pix * len(ALGOS) / t
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config({"sample_pixels": n_pix}),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"first {n_pix} pixels of the cube, all five algorithms"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = str(device_index)
+        try:
+            import torch
+            uuid = str(torch.cuda.get_device_properties(device_index).uuid)
+            self.dev = uuid if uuid.startswith("GPU-") else "GPU-" + uuid
+        except Exception:
+            vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+            if vis:
+                self.dev = vis.split(",")[device_index]
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", self.dev, f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- GPU leg
+def kernel_hash(name):
+    src = os.path.join(ROOT, "paper_2401_14762_gb300", "csrc", KERNEL_FILES[name])
+    return hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+
+
+def measured_traffic(name):
+    """Per-launch DRAM bytes from the committed ncu summary, if taken on this kernel source."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        rec = json.load(open(path))[name]
+    except Exception:
+        return None
+    if rec.get("source_sha256_16") != kernel_hash(name):
+        return None
+    return rec.get("dram_bytes_per_launch")
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+def run_gpu(args):
+    import torch
+
+    from paper_2401_14762_gb300 import build, cs
+    from paper_2401_14762_gb300 import synthetic as sy
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    build.build()
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+
+    # inputs of this rank's cube (pixels are independent: weak scaling over ranks)
+    seed = SEED + rank
+    Phi = sy.gaussian_phi(M, N, SEED)
+    Xt = sy.powerlaw_coeffs_torch(P, N, seed, dev)
+    E = sy.noise_torch(P, M, NOISE_VAR, seed, dev)
+    t0 = time.perf_counter()
+    ctx = cs.cs_create(M, N, Phi=Phi, admm_rho=RHO, stream=stream.cuda_stream)
+    setup_ms = (time.perf_counter() - t0) * 1e3
+    Y = torch.empty((P, M), device=dev)
+    outs = {a: torch.empty((P, N), device=dev) for a in ALGOS}
+    iters = {a: torch.zeros(P, device=dev, dtype=torch.int32) for a in ALGOS}
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    opts = {a: cs.make_opts(eps=EPS, max_iters=100, mu=MU, iters_out=iters[a]) for a in ALGOS}
+
+    def step(ev=None):
+        def mark(k):
+            if ev is not None:
+                ev[k].record(stream)
+        mark("start")
+        cs.cs_measure(ctx, Xt, Y, E)
+        mark("measure")
+        cs.cs_recover_fista(ctx, Y, outs["fista"], LAM, ITERS, opts["fista"])
+        mark("fista")
+        cs.cs_recover_admm(ctx, Y, outs["admm"], RHO, LAM, ITERS, opts["admm"])
+        mark("admm")
+        cs.cs_recover_gomp(ctx, Y, outs["gomp"], KAPPA, G, opts["gomp"])
+        mark("gomp")
+        cs.cs_recover_biht(ctx, Y, outs["biht"], KAPPA, opts["biht"])
+        mark("biht")
+        cs.cs_recover_cosamp(ctx, Y, outs["cosamp"], KAPPA, opts["cosamp"])
+        mark("cosamp")
+
+    for _ in range(args.warmup):
+        step()
+    cs.cs_sync(ctx)
+    names = ["start", "measure"] + ALGOS
+    per = {k: [] for k in names[1:]}
+    step_ms = []
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        wall0 = time.perf_counter()
+        for _ in range(args.steps):
+            flush.fill_(1)  # evict L2 between steps (outside the timed events)
+            ev = {k: torch.cuda.Event(enable_timing=True) for k in names}
+            step(ev)
+            torch.cuda.synchronize()
+            prev = "start"
+            for k in names[1:]:
+                per[k].append(ev[prev].elapsed_time(ev[k]))
+                prev = k
+            step_ms.append(ev["start"].elapsed_time(ev["cosamp"]))
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - wall0
+    if dist:
+        dist.barrier()
+    cs.cs_sync(ctx)
+    t_step = sum(step_ms) / len(step_ms)
+    if dist:
+        tt = torch.tensor([t_step], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_step = float(tt.item())
+    value = P * len(ALGOS) * world / (t_step * 1e-3)
+    kern_ms = {k: sum(v) / len(v) for k, v in per.items()}
+
+    # ---- end to end: pinned host buffers through the same C calls; the library copies
+    # every input in and every result out inside the timed region
+    Xh = Xt.cpu().pin_memory()
+    Eh = E.cpu().pin_memory()
+    Yh = torch.empty((P, M)).pin_memory()
+    outh = {a: torch.empty((P, N)).pin_memory() for a in ALGOS}
+    e2e_ms = []
+    for _ in range(max(1, min(args.steps, 2))):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        cs.cs_measure(ctx, Xh, Yh, Eh)
+        cs.cs_recover_fista(ctx, Yh, outh["fista"], LAM, ITERS, cs.make_opts(eps=EPS))
+        cs.cs_recover_admm(ctx, Yh, outh["admm"], RHO, LAM, ITERS, cs.make_opts(eps=EPS))
+        cs.cs_recover_gomp(ctx, Yh, outh["gomp"], KAPPA, G, cs.make_opts(eps=EPS))
+        cs.cs_recover_biht(ctx, Yh, outh["biht"], KAPPA, cs.make_opts(eps=EPS, mu=MU))
+        cs.cs_recover_cosamp(ctx, Yh, outh["cosamp"], KAPPA, cs.make_opts(eps=EPS))
+        e2e_ms.append((time.perf_counter() - t0) * 1e3)
+    e2e_t = sum(e2e_ms) / len(e2e_ms)
+    h2d = P * N * 4 + P * M * 4 + len(ALGOS) * P * M * 4
+    d2h = P * M * 4 + len(ALGOS) * P * N * 4
+
+    line = None
+    if rank == 0:
+        its = {a: iters[a].double().sum().item() for a in ALGOS}
+        # roofline of the dominant kernel (algorithmic flops per launch / event time)
+        flops = {"fista": 4.0 * M * N * its["fista"],
+                 "admm": (4.0 * M * N + 2.0 * M * M) * its["admm"],
+                 "measure": 2.0 * M * N * P}
+        dom = max(kern_ms, key=kern_ms.get)
+        pk = peaks()
+        roof = None
+        if dom in flops:
+            ach = flops[dom] / (kern_ms[dom] * 1e-3) / 1e12
+            roof = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": FP32_PEAK_TFLOPS,
+                    "unit": "TFLOP/s", "frac": ach / FP32_PEAK_TFLOPS,
+                    "traffic": measured_traffic(dom),
+                    "peak_kind": "derived FP32 FMA peak: 152 SMs x 128 lanes x 2 x 2070 MHz"}
+        else:
+            roof = {"kernel": dom, "bound": "alu", "achieved": None, "peak": FP64_PEAK_TFLOPS,
+                    "unit": "TFLOP/s", "frac": None, "traffic": measured_traffic(dom),
+                    "peak_kind": "FP64 nominal"}
+        kernels = {}
+        for k, ms in kern_ms.items():
+            ent = {"ms": ms, "share": ms / t_step}
+            if k in flops:
+                ach = flops[k] / (ms * 1e-3) / 1e12
+                ent.update(tflops=ach, frac_fp32_peak=ach / FP32_PEAK_TFLOPS)
+            if k in its:
+                ent["mean_iters"] = its[k] / P
+            kernels[k] = ent
+
+        # accuracy against the oracle on a sample, and the CPU baseline
+        n_s = 512
+        cores = host_cores()
+        Phi_s, Xs, Es = Phi, Xt[:n_s].double().cpu().numpy(), E[:n_s].double().cpu().numpy()
+        ref, secs = oracle_sample(n_s, cores, Xs, Es, Phi_s)
+        acc = {}
+        for a in ALGOS:
+            g = outs[a][:n_s].double().cpu().numpy()
+            r = ref[a] if a in ("fista", "admm") else ref[a][0]
+            acc[a] = float(np.linalg.norm(g - r) / np.linalg.norm(r))
+        cpu_value = n_s * len(ALGOS) / secs
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_step,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32", "data": "synthetic",
+                "config": config({"setup_ms": setup_ms, "wall_ms_per_step": wall * 1e3 / args.steps}),
+                "roofline": roof,
+                "cpu_baseline": {"value": cpu_value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                 "sample": f"first {n_s} pixels of the cube, all five algorithms, "
+                                           f"{secs:.1f} s"},
+                "e2e": {"value": P * len(ALGOS) / (e2e_t * 1e-3), "unit": UNIT,
+                        "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+                "gpu_launches": 6 * args.steps,
+                "clocks": clk.summary(),
+                "kernels": kernels,
+                "accuracy_rel_l2_vs_oracle": acc,
+                "peaks_file": {k: pk.get(k) for k in ("hbm_gbs", "bf16_tflops")}}
+        print(json.dumps(line), flush=True)
+    cs.cs_destroy(ctx)
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

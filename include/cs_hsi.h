@@ -1,0 +1,148 @@
+/*
+ * cs_hsi.h -- C ABI of libcs_hsi.so: per-pixel sparse recovery of a compressively
+ * sensed hyperspectral cube on one NVIDIA GB300 (sm_103a).
+ *
+ * Problem (Justo et al., "A Comparative Study of Compressive Sensing Algorithms for
+ * Hyperspectral Imaging Reconstruction", Section II, Eq. 1): every pixel's N-band
+ * spectrum is f = Psi x with x (nearly) sparse; the sensor records y = Phi f = A x with
+ * A = Phi Psi (M x N, M < N).  All P pixels of a cube share A.  The recovery calls
+ * run one of the paper's five algorithms (Section II-A, Algorithms 1-5) on every pixel.
+ *
+ * Conventions (all entry points):
+ *   - Matrices are row-major.  A cube is pixel-major: Y is P x M (Y[p*M + m]) and
+ *     X is P x N (X[p*N + n]), float32.  X holds the coefficient vectors x.
+ *   - Limits: 1 <= M <= N, M <= 128, N <= 256 (spectral dimension of one pixel).
+ *   - Y and X may be device pointers (cudaMalloc / torch) or host pointers (pageable or
+ *     pinned).  With device pointers the call is asynchronous on the context's stream.
+ *     With host pointers the library stages the cube through device buffers it owns,
+ *     copies on its stream and synchronises before returning.  Both must be of the
+ *     same kind.  Optional per-pixel outputs in cs_opts are always device pointers.
+ *   - Argument errors are reported synchronously, before anything is launched.
+ *   - Device-side conditions (non-finite input, a least-squares system that is not
+ *     positive definite, an iteration budget that ran out in a bounded wait) are
+ *     latched in a per-context status word; cs_sync() returns and clears it.
+ *   - The caller owns Y, X and the per-pixel output arrays; the context owns A, its
+ *     casts and factorisations and any staging buffers.  A context is not
+ *     thread-safe; use one per host thread.
+ */
+#ifndef CS_HSI_H
+#define CS_HSI_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct cs_ctx cs_ctx;
+
+typedef enum {
+  CS_OK = 0,
+  CS_ERR_ARG = 1,        /* invalid scalar argument or NULL pointer */
+  CS_ERR_SHAPE = 2,      /* M, N or P outside the supported range */
+  CS_ERR_CUDA = 3,       /* a CUDA runtime call failed (see cs_last_error) */
+  CS_ERR_OOM = 4,        /* device allocation failed */
+  CS_ERR_NOT_SPD = 5,    /* a support least-squares system was not positive definite */
+  CS_ERR_TIMEOUT = 6,    /* a bounded device wait ran out */
+  CS_ERR_NONFINITE = 7,  /* NaN or Inf in the measurements */
+  CS_ERR_NO_DEVICE = 8   /* no CUDA device of compute capability 10.3 */
+} cs_status;
+
+/* Arithmetic of the correlation products A z and A^T r.  CS_FP32 is the plain FP32
+ * path.  The others run the correlation on the tensor cores and win accuracy back
+ * with an FP32 residual recompute and a refinement pass (see each call). */
+typedef enum { CS_FP32 = 0, CS_BF16 = 1, CS_FP8_E4M3 = 2 } cs_precision;
+
+/* Options shared by the recovery calls; pass NULL for the defaults. */
+typedef struct {
+  /* Stopping tolerance on Delta = ||r^i - r^{i-1}||_2 (Section II-A and every
+   * algorithm's step 4/5).  Default 1e-8, the paper's epsilon (Section III).
+   * 0 runs a fixed number of iterations. */
+  double eps;
+  /* Iteration cap for BIHT and CoSaMP (default 100) and an extra cap for gOMP,
+   * whose own cap is min(kappa, floor(M/G)).  FISTA and ADMM take theirs as a call
+   * argument. */
+  int max_iters;
+  cs_precision prec;       /* default CS_FP32 */
+  double mu;               /* BIHT gradient step (Algorithm 4); default 0.1 (Section III) */
+  int32_t *iters_out;      /* optional, device, P entries: iterations each pixel ran */
+  uint8_t *converged_out;  /* optional, device, P entries: 1 if Delta < eps was reached,
+                              0 if the cap stopped it, 2 if its support LS failed */
+  const int16_t *kappa_per_pixel; /* optional, device, P entries: per-pixel sparsity
+                                     for the greedy calls (overrides kappa) */
+} cs_opts;
+
+/* Fills *opts with the defaults listed above. */
+void cs_opts_default(cs_opts *opts);
+
+/* Creates a context for an M x N dictionary (Eq. 1) on the current CUDA device.
+ *   A_host:   M x N row-major FP64 dictionary A = Phi Psi, or NULL to build it from
+ *   Phi_host: M x N row-major FP64 measurement matrix, and
+ *   Psi_host: N x N row-major FP64 sparsifying basis (f = Psi x), or NULL for the
+ *             orthonormal DCT-II basis, Psi[n][k] = a_k cos(pi (2n+1) k / 2N).
+ *   admm_rho: ADMM penalty alpha (Algorithm 2) to factor ahead of time; 0 to skip.
+ *   stream:   cudaStream_t every call of this context runs on (NULL = legacy default).
+ * On the device, in FP64: A = Phi Psi, the Gram matrix A^T A, the Lipschitz constant
+ * L = lambda_max(A^T A) (Section II-A) and, for ADMM, (A A^T + alpha I)^{-1}.
+ * Host arrays are only read during the call.  Blocks until the setup has finished. */
+cs_status cs_create(cs_ctx **out, int M, int N, const double *A_host, const double *Phi_host,
+                    const double *Psi_host, double admm_rho, void *stream);
+
+/* Releases the context and all device memory it owns. */
+void cs_destroy(cs_ctx *ctx);
+
+/* L = lambda_max(A^T A), the FISTA step constant (Section II-A). */
+cs_status cs_get_lipschitz(const cs_ctx *ctx, double *L);
+
+/* Copies the FP64 dictionary A (M x N, row-major) the context built into A_host. */
+cs_status cs_get_dictionary(const cs_ctx *ctx, double *A_host);
+
+/* Measurement, Eq. 1: Y[p] = A X[p] (+ E[p]) for p < P.  X: P x N, Y: P x M, E: P x M
+ * additive noise or NULL (the same kind of memory as X and Y).  FP32 arithmetic. */
+cs_status cs_measure(cs_ctx *ctx, const float *X, float *Y, const float *E, int64_t P);
+
+/* FISTA, Algorithm 1: x^0 = z^0 = 0, t^0 = 1; per iteration
+ *   x = soft(z - A^T(A z - y)/L, lambda/L), t' = (1 + sqrt(1 + 4t^2))/2,
+ *   z = x + ((t-1)/t')(x - x_prev), Delta = ||A x - A x_prev||;
+ * until Delta < opts->eps or `iters` iterations.  lambda >= 0, iters >= 0.
+ * prec = CS_BF16 runs A^T(A z - y) on the tensor cores with A z recomputed in FP32
+ * accuracy (split operands) and A^T applied to the small residual in BF16. */
+cs_status cs_recover_fista(cs_ctx *ctx, const float *Y, float *X, int64_t P, double lambda,
+                           int iters, const cs_opts *opts);
+
+/* ADMM, Algorithm 2 with the soft threshold lambda/rho (the scaled form whose fixed
+ * point is the Eq. 2 LASSO solution): x^0 = z^0 = w^0 = 0; per iteration
+ *   x = (A^T A + rho I)^{-1}(A^T y + rho (z - w)), z = soft(x + w, lambda/rho),
+ *   w = w + x - z, Delta = ||A x - A x_prev||;
+ * until Delta < opts->eps or `iters` iterations.  rho > 0, lambda >= 0.  Returns x. */
+cs_status cs_recover_admm(cs_ctx *ctx, const float *Y, float *X, int64_t P, double rho,
+                          double lambda, int iters, const cs_opts *opts);
+
+/* gOMP, Algorithm 3: per iteration select the G largest |A^T r|, add them to the
+ * support c, solve least squares on c, keep the kappa largest coefficients q, solve
+ * least squares on q, r = y - A x.  At most min(kappa, floor(M/G), max_iters)
+ * iterations.  1 <= G <= N, 0 <= kappa <= N.  G = 0 with kappa_per_pixel selects
+ * G = max(1, floor(kappa_p / 5)) per pixel (Section III's rule). */
+cs_status cs_recover_gomp(cs_ctx *ctx, const float *Y, float *X, int64_t P, int kappa, int G,
+                          const cs_opts *opts);
+
+/* BIHT (backtracking IHT), Algorithm 4: u = x + mu A^T(y - A x), c = supp(x) U the
+ * kappa largest |u|, least squares on c, keep the kappa largest coefficients. */
+cs_status cs_recover_biht(cs_ctx *ctx, const float *Y, float *X, int64_t P, int kappa,
+                          const cs_opts *opts);
+
+/* CoSaMP, Algorithm 5: c = c U the 2 kappa largest |A^T r|, least squares on c, keep
+ * the kappa largest coefficients (no refit), r = y - A x.  0 <= 2 kappa <= N. */
+cs_status cs_recover_cosamp(cs_ctx *ctx, const float *Y, float *X, int64_t P, int kappa,
+                            const cs_opts *opts);
+
+/* Waits for the context's stream and returns (and clears) the latched device status. */
+cs_status cs_sync(cs_ctx *ctx);
+
+/* Message of the last error on this thread ("" if none). */
+const char *cs_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CS_HSI_H */

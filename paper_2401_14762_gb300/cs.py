@@ -1,0 +1,246 @@
+"""ctypes binding of libcs_hsi.so with the C ABI's call names (include/cs_hsi.h).
+
+Argument marshalling only: arrays are torch tensors (CUDA or CPU) or numpy arrays,
+passed to the library as raw pointers; every step of the recovery runs in the
+library's CUDA kernels.  There is no CPU fallback: if the library is not built, or
+there is no GB300, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libcs_hsi.so")
+
+CS_OK, CS_ERR_ARG, CS_ERR_SHAPE, CS_ERR_CUDA, CS_ERR_OOM = 0, 1, 2, 3, 4
+CS_ERR_NOT_SPD, CS_ERR_TIMEOUT, CS_ERR_NONFINITE, CS_ERR_NO_DEVICE = 5, 6, 7, 8
+CS_FP32, CS_BF16, CS_FP8_E4M3 = 0, 1, 2
+
+EXPORTED = ["cs_opts_default", "cs_create", "cs_destroy", "cs_get_lipschitz", "cs_get_dictionary",
+            "cs_measure", "cs_recover_fista", "cs_recover_admm", "cs_recover_gomp",
+            "cs_recover_biht", "cs_recover_cosamp", "cs_sync", "cs_last_error"]
+
+
+class CsError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"cs status {status}: {msg}")
+        self.status = status
+
+
+class cs_opts(ctypes.Structure):
+    _fields_ = [("eps", ctypes.c_double), ("max_iters", ctypes.c_int), ("prec", ctypes.c_int),
+                ("mu", ctypes.c_double), ("iters_out", ctypes.c_void_p),
+                ("converged_out", ctypes.c_void_p), ("kappa_per_pixel", ctypes.c_void_p)]
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Loads libcs_hsi.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with "
+                           "`python -m paper_2401_14762_gb300.build` (needs nvcc)")
+    lib = ctypes.CDLL(path)
+    vp, i32, i64, dbl = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double
+    op = ctypes.POINTER(cs_opts)
+    lib.cs_opts_default.argtypes = [op]
+    lib.cs_opts_default.restype = None
+    lib.cs_create.argtypes = [ctypes.POINTER(vp), i32, i32, vp, vp, vp, dbl, vp]
+    lib.cs_destroy.argtypes = [vp]
+    lib.cs_destroy.restype = None
+    lib.cs_get_lipschitz.argtypes = [vp, ctypes.POINTER(dbl)]
+    lib.cs_get_dictionary.argtypes = [vp, vp]
+    lib.cs_measure.argtypes = [vp, vp, vp, vp, i64]
+    lib.cs_recover_fista.argtypes = [vp, vp, vp, i64, dbl, i32, op]
+    lib.cs_recover_admm.argtypes = [vp, vp, vp, i64, dbl, dbl, i32, op]
+    lib.cs_recover_gomp.argtypes = [vp, vp, vp, i64, i32, i32, op]
+    lib.cs_recover_biht.argtypes = [vp, vp, vp, i64, i32, op]
+    lib.cs_recover_cosamp.argtypes = [vp, vp, vp, i64, i32, op]
+    lib.cs_sync.argtypes = [vp]
+    lib.cs_last_error.argtypes = []
+    lib.cs_last_error.restype = ctypes.c_char_p
+    for name in EXPORTED:
+        if name not in ("cs_opts_default", "cs_destroy", "cs_last_error"):
+            getattr(lib, name).restype = i32
+    _lib = lib
+    return lib
+
+
+def _check(status: int):
+    if status != CS_OK:
+        raise CsError(status, load_library().cs_last_error().decode())
+
+
+def _ptr(a, dtype=None):
+    """Raw pointer of a contiguous torch tensor or numpy array (None -> NULL)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        if dtype is not None and a.dtype != dtype:
+            raise TypeError(f"expected {dtype}, got {a.dtype}")
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return a.ctypes.data
+    import torch
+    if isinstance(a, torch.Tensor):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        if dtype is not None and a.dtype != {np.float32: torch.float32, np.float64: torch.float64,
+                                            np.int32: torch.int32, np.uint8: torch.uint8,
+                                            np.int16: torch.int16}[dtype]:
+            raise TypeError(f"expected {dtype}, got {a.dtype}")
+        return a.data_ptr()
+    raise TypeError(f"unsupported array type {type(a)}")
+
+
+def _default_stream():
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return torch.cuda.current_stream().cuda_stream
+    except Exception:
+        pass
+    return None
+
+
+class Context:
+    """Owns a cs_ctx handle (released by cs_destroy / close())."""
+
+    def __init__(self, handle, M, N):
+        self.handle, self.M, self.N = handle, M, N
+
+    def close(self):
+        if self.handle:
+            load_library().cs_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def cs_opts_default() -> cs_opts:
+    o = cs_opts()
+    load_library().cs_opts_default(ctypes.byref(o))
+    return o
+
+
+def make_opts(eps=1e-8, max_iters=100, prec=CS_FP32, mu=0.1, iters_out=None,
+              converged_out=None, kappa_per_pixel=None) -> cs_opts:
+    o = cs_opts_default()
+    o.eps, o.max_iters, o.prec, o.mu = float(eps), int(max_iters), int(prec), float(mu)
+    o.iters_out = _ptr(iters_out, np.int32)
+    o.converged_out = _ptr(converged_out, np.uint8)
+    o.kappa_per_pixel = _ptr(kappa_per_pixel, np.int16)
+    return o
+
+
+def cs_create(M, N, A=None, Phi=None, Psi=None, admm_rho=0.0, stream=None) -> Context:
+    """Builds the FP64 dictionary A = Phi Psi (or takes A), its Gram matrix, the Lipschitz
+    constant and optionally the ADMM factor on the device (Eq. 1, Section II-A)."""
+    lib = load_library()
+    keep = []
+
+    def host64(a):
+        if a is None:
+            return None
+        a = np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+        keep.append(a)
+        return a.ctypes.data
+
+    h = ctypes.c_void_p()
+    st = lib.cs_create(ctypes.byref(h), int(M), int(N), host64(A), host64(Phi), host64(Psi),
+                       float(admm_rho), stream if stream is not None else _default_stream())
+    _check(st)
+    return Context(h.value, int(M), int(N))
+
+
+def cs_destroy(ctx: Context):
+    ctx.close()
+
+
+def cs_get_lipschitz(ctx: Context) -> float:
+    L = ctypes.c_double()
+    _check(load_library().cs_get_lipschitz(ctx.handle, ctypes.byref(L)))
+    return L.value
+
+
+def cs_get_dictionary(ctx: Context) -> np.ndarray:
+    A = np.empty((ctx.M, ctx.N))
+    _check(load_library().cs_get_dictionary(ctx.handle, A.ctypes.data))
+    return A
+
+
+def _rows(a):
+    return int(a.shape[0])
+
+
+def cs_measure(ctx: Context, X, Y, E=None, P=None):
+    """Y = X A^T (+ E) (Eq. 1)."""
+    P = _rows(X) if P is None else P
+    _check(load_library().cs_measure(ctx.handle, _ptr(X, np.float32), _ptr(Y, np.float32),
+                                     _ptr(E, np.float32), int(P)))
+    return Y
+
+
+def cs_recover_fista(ctx: Context, Y, X, lam, iters, opts: cs_opts | None = None, P=None):
+    P = _rows(Y) if P is None else P
+    _check(load_library().cs_recover_fista(ctx.handle, _ptr(Y, np.float32), _ptr(X, np.float32),
+                                           int(P), float(lam), int(iters),
+                                           ctypes.byref(opts) if opts else None))
+    return X
+
+
+def cs_recover_admm(ctx: Context, Y, X, rho, lam, iters, opts: cs_opts | None = None, P=None):
+    P = _rows(Y) if P is None else P
+    _check(load_library().cs_recover_admm(ctx.handle, _ptr(Y, np.float32), _ptr(X, np.float32),
+                                          int(P), float(rho), float(lam), int(iters),
+                                          ctypes.byref(opts) if opts else None))
+    return X
+
+
+def cs_recover_gomp(ctx: Context, Y, X, kappa, G, opts: cs_opts | None = None, P=None):
+    P = _rows(Y) if P is None else P
+    _check(load_library().cs_recover_gomp(ctx.handle, _ptr(Y, np.float32), _ptr(X, np.float32),
+                                          int(P), int(kappa), int(G),
+                                          ctypes.byref(opts) if opts else None))
+    return X
+
+
+def cs_recover_biht(ctx: Context, Y, X, kappa, opts: cs_opts | None = None, P=None):
+    P = _rows(Y) if P is None else P
+    _check(load_library().cs_recover_biht(ctx.handle, _ptr(Y, np.float32), _ptr(X, np.float32),
+                                          int(P), int(kappa),
+                                          ctypes.byref(opts) if opts else None))
+    return X
+
+
+def cs_recover_cosamp(ctx: Context, Y, X, kappa, opts: cs_opts | None = None, P=None):
+    P = _rows(Y) if P is None else P
+    _check(load_library().cs_recover_cosamp(ctx.handle, _ptr(Y, np.float32), _ptr(X, np.float32),
+                                            int(P), int(kappa),
+                                            ctypes.byref(opts) if opts else None))
+    return X
+
+
+def cs_sync(ctx: Context):
+    _check(load_library().cs_sync(ctx.handle))
+
+
+def cs_last_error() -> str:
+    return load_library().cs_last_error().decode()

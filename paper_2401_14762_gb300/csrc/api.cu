@@ -1,0 +1,359 @@
+// C ABI of libcs_hsi.so (declared in include/cs_hsi.h): argument checks, context
+// lifetime, host-pointer staging and dispatch to the device kernels.
+#include <cuda_runtime.h>
+#include <stdio.h>
+
+#include <cmath>
+#include <new>
+#include <string>
+
+#include "cs_hsi.h"
+#include "cs_internal.cuh"
+
+struct cs_ctx {
+  cs::Ctx c;
+};
+
+namespace cs {
+
+static thread_local std::string g_err;
+
+void set_error(const std::string& msg) { g_err = msg; }
+
+cs_status cuda_fail(cudaError_t e, const char* what) {
+  set_error(std::string(what) + ": " + cudaGetErrorString(e));
+  return e == cudaErrorMemoryAllocation ? CS_ERR_OOM : CS_ERR_CUDA;
+}
+
+namespace {
+
+cs_status arg_error(const char* msg) {
+  set_error(msg);
+  return CS_ERR_ARG;
+}
+
+template <typename T>
+cudaError_t dalloc(T** p, size_t elems) {
+  return cudaMalloc(reinterpret_cast<void**>(p), sizeof(T) * (elems ? elems : 1));
+}
+
+void free_ctx(Ctx& c) {
+  cudaFree(c.A64);
+  cudaFree(c.At64);
+  cudaFree(c.G64);
+  cudaFree(c.A32);
+  cudaFree(c.At32);
+  cudaFree(c.W32);
+  cudaFree(c.scratch64);
+  cudaFree(c.status);
+  cudaFree(c.counter);
+  cudaFree(c.stage_in);
+  cudaFree(c.stage_out);
+  cudaFree(c.stage_aux);
+}
+
+// Is ptr device-accessible memory (cudaMalloc / managed)?  Host memory, pinned or not,
+// goes through the staging path.
+bool is_device_ptr(const void* ptr) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, ptr) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+cudaError_t ensure_stage(float** buf, size_t* have, size_t bytes) {
+  if (*have >= bytes) return cudaSuccess;
+  cudaFree(*buf);
+  *buf = nullptr;
+  *have = 0;
+  cudaError_t e = cudaMalloc(reinterpret_cast<void**>(buf), bytes ? bytes : 16);
+  if (e == cudaSuccess) *have = bytes;
+  return e;
+}
+
+cs_status check_ctx(const cs_ctx* ctx) {
+  if (!ctx) return arg_error("ctx is NULL");
+  return CS_OK;
+}
+
+// Runs `fn(Y_dev, X_dev)` on device buffers; host buffers are staged and copied back.
+template <typename F>
+cs_status with_cube(cs_ctx* ctx, const float* Y, float* X, int64_t P, int in_cols, int out_cols,
+                    F fn) {
+  Ctx& c = ctx->c;
+  bool dy = is_device_ptr(Y), dx = is_device_ptr(X);
+  if (dy != dx) return arg_error("input and output must both be device or both be host memory");
+  if (dy) {
+    cudaError_t e = fn(Y, X);
+    if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
+    return CS_OK;
+  }
+  size_t bin = sizeof(float) * (size_t)P * in_cols, bout = sizeof(float) * (size_t)P * out_cols;
+  cudaError_t e = ensure_stage(&c.stage_in, &c.stage_in_bytes, bin);
+  if (e == cudaSuccess) e = ensure_stage(&c.stage_out, &c.stage_out_bytes, bout);
+  if (e != cudaSuccess) return cuda_fail(e, "staging allocation");
+  e = cudaMemcpyAsync(c.stage_in, Y, bin, cudaMemcpyHostToDevice, c.stream);
+  if (e != cudaSuccess) return cuda_fail(e, "host-to-device copy");
+  e = fn(c.stage_in, c.stage_out);
+  if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
+  e = cudaMemcpyAsync(X, c.stage_out, bout, cudaMemcpyDeviceToHost, c.stream);
+  if (e != cudaSuccess) return cuda_fail(e, "device-to-host copy");
+  e = cudaStreamSynchronize(c.stream);
+  if (e != cudaSuccess) return cuda_fail(e, "stream synchronize");
+  return CS_OK;
+}
+
+}  // namespace
+}  // namespace cs
+
+using cs::arg_error;
+using cs::cuda_fail;
+
+extern "C" {
+
+void cs_opts_default(cs_opts* o) {
+  if (!o) return;
+  o->eps = 1e-8;
+  o->max_iters = 100;
+  o->prec = CS_FP32;
+  o->mu = 0.1;
+  o->iters_out = nullptr;
+  o->converged_out = nullptr;
+  o->kappa_per_pixel = nullptr;
+}
+
+const char* cs_last_error(void) { return cs::g_err.c_str(); }
+
+cs_status cs_create(cs_ctx** out, int M, int N, const double* A_host, const double* Phi_host,
+                    const double* Psi_host, double admm_rho, void* stream) {
+  cs::set_error("");
+  if (!out) return arg_error("out is NULL");
+  *out = nullptr;
+  if (M < 1 || N < 1 || M > N || M > cs::kMaxM || N > cs::kMaxN) {
+    cs::set_error("need 1 <= M <= N, M <= 128, N <= 256");
+    return CS_ERR_SHAPE;
+  }
+  if (!A_host && !Phi_host) return arg_error("give A or Phi");
+  if (!(admm_rho >= 0.0) || !std::isfinite(admm_rho)) return arg_error("admm_rho must be >= 0");
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) {
+    cs::set_error(std::string("no CUDA device: ") + cudaGetErrorString(e));
+    return CS_ERR_NO_DEVICE;
+  }
+  cudaDeviceProp prop;
+  e = cudaGetDeviceProperties(&prop, dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDeviceProperties");
+  if (prop.major != 10 || prop.minor != 3) {
+    cs::set_error("libcs_hsi is built for compute capability 10.3 (GB300)");
+    return CS_ERR_NO_DEVICE;
+  }
+  cs_ctx* ctx = new (std::nothrow) cs_ctx();
+  if (!ctx) return CS_ERR_OOM;
+  cs::Ctx& c = ctx->c;
+  c.M = M;
+  c.N = N;
+  c.device = dev;
+  c.num_sms = prop.multiProcessorCount;
+  c.stream = static_cast<cudaStream_t>(stream);
+  c.scratch_elems = (size_t)M * N + (size_t)N * N + 3 * (size_t)M * M + cs::kMaxM + 8;
+  if ((e = cs::dalloc(&c.A64, (size_t)M * N)) != cudaSuccess ||
+      (e = cs::dalloc(&c.At64, (size_t)N * M)) != cudaSuccess ||
+      (e = cs::dalloc(&c.G64, (size_t)N * N)) != cudaSuccess ||
+      (e = cs::dalloc(&c.A32, (size_t)M * N)) != cudaSuccess ||
+      (e = cs::dalloc(&c.At32, (size_t)N * M)) != cudaSuccess ||
+      (e = cs::dalloc(&c.W32, (size_t)M * M)) != cudaSuccess ||
+      (e = cs::dalloc(&c.scratch64, c.scratch_elems)) != cudaSuccess ||
+      (e = cs::dalloc(&c.status, 1)) != cudaSuccess ||
+      (e = cs::dalloc(&c.counter, 2)) != cudaSuccess) {
+    cs::free_ctx(c);
+    delete ctx;
+    return cuda_fail(e, "cs_create allocation");
+  }
+  cudaMemsetAsync(c.status, 0, sizeof(int), c.stream);
+  e = cs::setup_dictionary(c, A_host, Phi_host, Psi_host);
+  if (e == cudaSuccess && admm_rho > 0.0) e = cs::setup_admm_factor(c, admm_rho);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c.stream);
+  if (e != cudaSuccess) {
+    cs::free_ctx(c);
+    delete ctx;
+    return cuda_fail(e, "cs_create setup");
+  }
+  *out = ctx;
+  return CS_OK;
+}
+
+void cs_destroy(cs_ctx* ctx) {
+  if (!ctx) return;
+  cudaStreamSynchronize(ctx->c.stream);
+  cs::free_ctx(ctx->c);
+  delete ctx;
+}
+
+cs_status cs_get_lipschitz(const cs_ctx* ctx, double* L) {
+  if (cs_status s = cs::check_ctx(ctx)) return s;
+  if (!L) return arg_error("L is NULL");
+  *L = ctx->c.L;
+  return CS_OK;
+}
+
+cs_status cs_get_dictionary(const cs_ctx* ctx, double* A_host) {
+  if (cs_status s = cs::check_ctx(ctx)) return s;
+  if (!A_host) return arg_error("A_host is NULL");
+  const cs::Ctx& c = ctx->c;
+  cudaError_t e = cudaMemcpyAsync(A_host, c.A64, sizeof(double) * c.M * c.N,
+                                  cudaMemcpyDeviceToHost, c.stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c.stream);
+  if (e != cudaSuccess) return cuda_fail(e, "cs_get_dictionary");
+  return CS_OK;
+}
+
+cs_status cs_measure(cs_ctx* ctx, const float* X, float* Y, const float* E, int64_t P) {
+  if (cs_status s = cs::check_ctx(ctx)) return s;
+  if (P < 0) return arg_error("P < 0");
+  if (P == 0) return CS_OK;
+  if (!X || !Y) return arg_error("X or Y is NULL");
+  cs::Ctx& c = ctx->c;
+  const float* Ed = E;
+  if (E && cs::is_device_ptr(E) != cs::is_device_ptr(X))
+    return arg_error("E must be the same kind of memory as X and Y");
+  if (E && !cs::is_device_ptr(E)) {  // host noise: staged like the cube
+    size_t bytes = sizeof(float) * (size_t)P * c.M;
+    cudaError_t e = cs::ensure_stage(&c.stage_aux, &c.stage_aux_bytes, bytes);
+    if (e != cudaSuccess) return cuda_fail(e, "staging allocation");
+    e = cudaMemcpyAsync(c.stage_aux, E, bytes, cudaMemcpyHostToDevice, c.stream);
+    if (e != cudaSuccess) return cuda_fail(e, "host-to-device copy");
+    Ed = c.stage_aux;
+  }
+  return cs::with_cube(ctx, X, Y, P, c.N, c.M, [&](const float* Xd, float* Yd) {
+    return cs::launch_measure(c, Xd, Yd, Ed, P);
+  });
+}
+
+static cs_status check_common(const cs_ctx* ctx, const float* Y, float* X, int64_t P,
+                              const cs_opts* o) {
+  if (cs_status s = cs::check_ctx(ctx)) return s;
+  if (P < 0) return arg_error("P < 0");
+  if (P > 0 && (!Y || !X)) return arg_error("Y or X is NULL");
+  if (P > ((int64_t)1 << 31) - 1) {
+    cs::set_error("P must be below 2^31");
+    return CS_ERR_SHAPE;
+  }
+  if (!(o->eps >= 0.0) || !std::isfinite(o->eps)) return arg_error("eps must be >= 0");
+  if (o->max_iters < 0) return arg_error("max_iters < 0");
+  if (o->prec != CS_FP32 && o->prec != CS_BF16 && o->prec != CS_FP8_E4M3)
+    return arg_error("unknown precision");
+  if ((o->iters_out && !cs::is_device_ptr(o->iters_out)) ||
+      (o->converged_out && !cs::is_device_ptr(o->converged_out)) ||
+      (o->kappa_per_pixel && !cs::is_device_ptr(o->kappa_per_pixel)))
+    return arg_error("per-pixel option arrays must be device memory");
+  return CS_OK;
+}
+
+cs_status cs_recover_fista(cs_ctx* ctx, const float* Y, float* X, int64_t P, double lambda,
+                           int iters, const cs_opts* opts) {
+  cs_opts o;
+  cs_opts_default(&o);
+  if (opts) o = *opts;
+  if (cs_status s = check_common(ctx, Y, X, P, &o)) return s;
+  if (!(lambda >= 0.0) || !std::isfinite(lambda)) return arg_error("lambda must be >= 0");
+  if (iters < 0) return arg_error("iters < 0");
+  if (P == 0) return CS_OK;
+  cs::Ctx& c = ctx->c;
+  return cs::with_cube(ctx, Y, X, P, c.M, c.N, [&](const float* Yd, float* Xd) {
+    cs::ConvexArgs a{Yd, Xd, P, lambda, 0.0, o.eps, iters, o.iters_out, o.converged_out, o.prec};
+    return cs::launch_fista(c, a);
+  });
+}
+
+cs_status cs_recover_admm(cs_ctx* ctx, const float* Y, float* X, int64_t P, double rho,
+                          double lambda, int iters, const cs_opts* opts) {
+  cs_opts o;
+  cs_opts_default(&o);
+  if (opts) o = *opts;
+  if (cs_status s = check_common(ctx, Y, X, P, &o)) return s;
+  if (!(rho > 0.0) || !std::isfinite(rho)) return arg_error("rho must be > 0");
+  if (!(lambda >= 0.0) || !std::isfinite(lambda)) return arg_error("lambda must be >= 0");
+  if (iters < 0) return arg_error("iters < 0");
+  if (P == 0) return CS_OK;
+  cs::Ctx& c = ctx->c;
+  if (c.rho != rho) {
+    cudaError_t e = cs::setup_admm_factor(c, rho);
+    if (e != cudaSuccess) return cuda_fail(e, "ADMM factor");
+  }
+  return cs::with_cube(ctx, Y, X, P, c.M, c.N, [&](const float* Yd, float* Xd) {
+    cs::ConvexArgs a{Yd, Xd, P, lambda, rho, o.eps, iters, o.iters_out, o.converged_out, o.prec};
+    return cs::launch_admm(c, a);
+  });
+}
+
+static cs_status greedy(cs_ctx* ctx, cs::GreedyAlgo algo, const float* Y, float* X, int64_t P,
+                        int kappa, int G, const cs_opts* opts) {
+  cs_opts o;
+  cs_opts_default(&o);
+  if (opts) o = *opts;
+  if (cs_status s = check_common(ctx, Y, X, P, &o)) return s;
+  cs::Ctx& c = ctx->c;
+  int kmax = kappa;
+  if (o.kappa_per_pixel) {
+    // the caller bounds the per-pixel levels by kappa (used to size the workspace)
+    if (kappa < 0 || kappa > c.N) return arg_error("kappa (upper bound) out of range");
+  } else if (kappa < 0 || kappa > c.N) {
+    return arg_error("kappa out of range");
+  }
+  if (algo == cs::kCosamp && 2 * kmax > c.N) return arg_error("CoSaMP needs 2 kappa <= N");
+  if (algo == cs::kGomp && (G < 0 || G > c.N || (G == 0 && !o.kappa_per_pixel)))
+    return arg_error("G must be in 1..N (0 only with kappa_per_pixel)");
+  if (algo == cs::kBiht && !std::isfinite(o.mu)) return arg_error("mu must be finite");
+  if (P == 0) return CS_OK;
+  return cs::with_cube(ctx, Y, X, P, c.M, c.N, [&](const float* Yd, float* Xd) {
+    cs::GreedyArgs a{Yd, Xd, P, kappa, G, o.mu, o.eps, o.max_iters, o.kappa_per_pixel, kmax,
+                     o.iters_out, o.converged_out, o.prec};
+    return cs::launch_greedy(c, algo, a);
+  });
+}
+
+cs_status cs_recover_gomp(cs_ctx* ctx, const float* Y, float* X, int64_t P, int kappa, int G,
+                          const cs_opts* opts) {
+  return greedy(ctx, cs::kGomp, Y, X, P, kappa, G, opts);
+}
+
+cs_status cs_recover_biht(cs_ctx* ctx, const float* Y, float* X, int64_t P, int kappa,
+                          const cs_opts* opts) {
+  return greedy(ctx, cs::kBiht, Y, X, P, kappa, 0, opts);
+}
+
+cs_status cs_recover_cosamp(cs_ctx* ctx, const float* Y, float* X, int64_t P, int kappa,
+                            const cs_opts* opts) {
+  return greedy(ctx, cs::kCosamp, Y, X, P, kappa, 0, opts);
+}
+
+cs_status cs_sync(cs_ctx* ctx) {
+  if (cs_status s = cs::check_ctx(ctx)) return s;
+  cs::Ctx& c = ctx->c;
+  cudaError_t e = cudaStreamSynchronize(c.stream);
+  if (e != cudaSuccess) return cuda_fail(e, "cs_sync");
+  int st = 0;
+  e = cudaMemcpy(&st, c.status, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(e, "cs_sync status read");
+  if (st) {
+    cudaMemset(c.status, 0, sizeof(int));
+    if (st & cs::kStNonFinite) {
+      cs::set_error("non-finite measurements");
+      return CS_ERR_NONFINITE;
+    }
+    if (st & cs::kStNotSpd) {
+      cs::set_error("a least-squares system was not positive definite");
+      return CS_ERR_NOT_SPD;
+    }
+    if (st & cs::kStTimeout) {
+      cs::set_error("a bounded device wait ran out");
+      return CS_ERR_TIMEOUT;
+    }
+  }
+  return CS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,557 @@
+// FP32 SIMT path: measurement (Eq. 1), FISTA (Algorithm 1) and ADMM (Algorithm 2).
+//
+// One CTA of 256 threads owns a tile of 32 pixels for the whole solve; the dictionary A
+// (M x N, FP32, rows padded) sits in shared memory and every pixel's iterate lives in
+// registers, so the only HBM traffic is Y in and X out.  Warp w owns pixels 4w..4w+3.
+//   * "column" mapping: lane l owns columns 4l..4l+3 (and 128+4l..128+4l+3 if N > 128)
+//     of the N-long vectors of its 4 pixels -- the A^T r products and the proximal step.
+//   * "row" mapping: lane l owns rows l, l+32, ... (< M) of the M-long vectors of its 4
+//     pixels -- the A x products, the residual and Delta.
+// Each product is a register-blocked outer-product loop over shared memory: per step a
+// lane reads one float4 of A per chunk and one broadcast float4 of the 4 pixels' operand.
+//
+// FISTA keeps u = A x so that A z = u + beta (u - u_prev) needs no extra product and
+// Delta = ||r^i - r^{i-1}|| = ||u^i - u^{i-1}|| comes for free: 4MN flops per iteration.
+// ADMM uses the Woodbury form of its x-step,
+//   (A^T A + rho I)^{-1} v = (v - A^T W A v) / rho,  W = (A A^T + rho I)^{-1},
+// which with d = z - w and h = W (y - A d) gives x = d + A^T h and A x = y - rho h, so
+// r^i = rho h^i: 4MN + 2M^2 flops per iteration, Delta again for free.
+#include <cuda_runtime.h>
+
+#include "cs_internal.cuh"
+
+namespace cs {
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kPPW = 4;   // pixels per warp
+constexpr int kT = 32;    // pixels per CTA
+constexpr int kLdv = 36;  // row stride of the M x T residual buffer (conflict-free float4)
+
+struct CvParams {
+  int M, N, Npad, lda, ldw, Mpad;
+  const float* A;  // M x N global
+  const float* W;  // M x M global (ADMM)
+  const float* Y;
+  float* X;
+  const float* E;  // measurement noise (measure only)
+  float* Yout;     // measurement output (measure only)
+  int64_t P;
+  float c1, c2;    // FISTA: 1/L, lambda/L.  ADMM: rho, lambda/rho
+  float eps2;      // eps^2 (0 => fixed iteration count)
+  int start_done;  // eps > 1: Delta = 1 < eps before the first iteration
+  int iters;
+  int32_t* iters_out;
+  uint8_t* conv_out;
+  int* status;
+};
+
+__device__ __forceinline__ float soft_thr(float a, float t) {
+  float m = fabsf(a) - t;
+  return m > 0.f ? copysignf(m, a) : 0.f;
+}
+
+__device__ __forceinline__ float f4(const float4& v, int e) {
+  return e == 0 ? v.x : (e == 1 ? v.y : (e == 2 ? v.z : v.w));
+}
+
+// rows x cols global matrix -> shared, row stride ld, zero padding in [cols, ld)
+__device__ void stage_matrix(float* dst, const float* src, int rows, int cols, int ld) {
+  for (int i = threadIdx.x; i < rows * ld; i += blockDim.x) {
+    int r = i / ld, c = i - r * ld;
+    dst[i] = c < cols ? src[r * cols + c] : 0.f;
+  }
+}
+
+// acc[i][j] += sum_k Ms[row_j][k] * Vs[(pix_i) * ldv_ + k]  (row mapping product)
+template <int MR>
+__device__ __forceinline__ void rows_product(float (&acc)[kPPW][MR], const float* Ms, int ldm,
+                                             const float* Vs, int ldv_, int kpad, int warp,
+                                             const int (&row)[MR], const bool (&hr)[MR]) {
+#pragma unroll
+  for (int i = 0; i < kPPW; ++i)
+#pragma unroll
+    for (int j = 0; j < MR; ++j) acc[i][j] = 0.f;
+  const float* vb = Vs + (warp * kPPW) * ldv_;
+#pragma unroll 2
+  for (int k = 0; k < kpad; k += 4) {
+    float4 xv[kPPW];
+#pragma unroll
+    for (int i = 0; i < kPPW; ++i) xv[i] = *reinterpret_cast<const float4*>(vb + i * ldv_ + k);
+#pragma unroll
+    for (int j = 0; j < MR; ++j) {
+      if (!hr[j]) continue;
+      float4 a = *reinterpret_cast<const float4*>(Ms + row[j] * ldm + k);
+#pragma unroll
+      for (int i = 0; i < kPPW; ++i)
+        acc[i][j] += xv[i].x * a.x + xv[i].y * a.y + xv[i].z * a.z + xv[i].w * a.w;
+    }
+  }
+}
+
+// acc[i][4c+e] = sum_m vs[m][pix_i] * As[m][col_c + e]  (column mapping product, A^T v)
+template <int NCH>
+__device__ __forceinline__ void cols_product(float (&acc)[kPPW][4 * NCH], const float* As,
+                                             int lda, const float* vs, int M, int warp,
+                                             const int (&col)[NCH], const bool (&hc)[NCH]) {
+#pragma unroll
+  for (int i = 0; i < kPPW; ++i)
+#pragma unroll
+    for (int k = 0; k < 4 * NCH; ++k) acc[i][k] = 0.f;
+  const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll 2
+  for (int m = 0; m < M; ++m) {
+    float4 v = *reinterpret_cast<const float4*>(vs + m * kLdv + warp * kPPW);
+#pragma unroll
+    for (int c = 0; c < NCH; ++c) {
+      float4 a = hc[c] ? *reinterpret_cast<const float4*>(As + m * lda + col[c]) : zero;
+#pragma unroll
+      for (int i = 0; i < kPPW; ++i) {
+        float vi = f4(v, i);
+        acc[i][4 * c + 0] += vi * a.x;
+        acc[i][4 * c + 1] += vi * a.y;
+        acc[i][4 * c + 2] += vi * a.z;
+        acc[i][4 * c + 3] += vi * a.w;
+      }
+    }
+  }
+}
+
+template <int NCH>
+__device__ __forceinline__ void write_x(float* X, int64_t pix, int N, const float (&x)[4 * NCH],
+                                        const int (&col)[NCH]) {
+#pragma unroll
+  for (int c = 0; c < NCH; ++c)
+#pragma unroll
+    for (int e = 0; e < 4; ++e)
+      if (col[c] + e < N) X[pix * N + col[c] + e] = x[4 * c + e];
+}
+
+// ---------------------------------------------------------------------------------
+// Algorithm 1 (FISTA)
+// ---------------------------------------------------------------------------------
+template <int MR, int NCH>
+__global__ void __launch_bounds__(kThreads, 1) k_fista_f32(CvParams p) {
+  extern __shared__ __align__(16) float sm[];
+  const int M = p.M, lda = p.lda;
+  float* As = sm;
+  float* xs = As + M * lda;
+  float* vs = xs + kT * lda;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int64_t pix0 = (int64_t)blockIdx.x * kT + warp * kPPW;
+
+  stage_matrix(As, p.A, M, p.N, lda);
+  for (int i = tid; i < kT * lda; i += kThreads) xs[i] = 0.f;
+
+  int col[NCH], row[MR];
+  bool hc[NCH], hr[MR];
+#pragma unroll
+  for (int c = 0; c < NCH; ++c) {
+    col[c] = 128 * c + 4 * lane;
+    hc[c] = col[c] < p.Npad;
+  }
+#pragma unroll
+  for (int j = 0; j < MR; ++j) {
+    row[j] = lane + 32 * j;
+    hr[j] = row[j] < M;
+  }
+  float yv[kPPW][MR], u[kPPW][MR], up[kPPW][MR];
+  float x[kPPW][4 * NCH], z[kPPW][4 * NCH];
+  bool done[kPPW];
+  bool bad = false;
+#pragma unroll
+  for (int i = 0; i < kPPW; ++i) {
+    bool valid = pix0 + i < p.P;
+    done[i] = !valid || p.start_done;
+#pragma unroll
+    for (int j = 0; j < MR; ++j) {
+      float v = (valid && hr[j]) ? p.Y[(pix0 + i) * M + row[j]] : 0.f;
+      bad |= !isfinite(v);
+      yv[i][j] = v;
+      u[i][j] = up[i][j] = 0.f;
+    }
+#pragma unroll
+    for (int k = 0; k < 4 * NCH; ++k) x[i][k] = z[i][k] = 0.f;
+  }
+  if (bad) atomicOr(p.status, kStNonFinite);
+  __syncthreads();
+
+  double t = 1.0;
+  float beta_prev = 0.f;
+  int it = 0;
+  // After A is staged the warps never synchronise: a warp owns its pixels in both
+  // mappings, so __syncwarp orders every shared-memory hand-off.
+  while (it < p.iters) {
+    if (done[0] && done[1] && done[2] && done[3]) break;  // warp-uniform
+    // residual of the extrapolated point: A z - y = u + beta (u - u_prev) - y
+#pragma unroll
+    for (int j = 0; j < MR; ++j) {
+      if (!hr[j]) continue;
+      float4 v;
+      v.x = u[0][j] + beta_prev * (u[0][j] - up[0][j]) - yv[0][j];
+      v.y = u[1][j] + beta_prev * (u[1][j] - up[1][j]) - yv[1][j];
+      v.z = u[2][j] + beta_prev * (u[2][j] - up[2][j]) - yv[2][j];
+      v.w = u[3][j] + beta_prev * (u[3][j] - up[3][j]) - yv[3][j];
+      *reinterpret_cast<float4*>(vs + row[j] * kLdv + warp * kPPW) = v;
+    }
+    __syncwarp();
+    // steps 1-4: aux = z - A^T(Az - y)/L, x = soft(aux, lambda/L), t, z
+    float acc[kPPW][4 * NCH];
+    cols_product<NCH>(acc, As, lda, vs, M, warp, col, hc);
+    double tn = 0.5 * (1.0 + sqrt(1.0 + 4.0 * t * t));
+    float beta = (float)((t - 1.0) / tn);
+    t = tn;
+#pragma unroll
+    for (int i = 0; i < kPPW; ++i) {
+      if (done[i]) continue;
+#pragma unroll
+      for (int k = 0; k < 4 * NCH; ++k) {
+        float xn = soft_thr(z[i][k] - acc[i][k] * p.c1, p.c2);
+        z[i][k] = xn + beta * (xn - x[i][k]);
+        x[i][k] = xn;
+      }
+#pragma unroll
+      for (int c = 0; c < NCH; ++c)
+        if (hc[c])
+          *reinterpret_cast<float4*>(xs + (warp * kPPW + i) * lda + col[c]) =
+              make_float4(x[i][4 * c], x[i][4 * c + 1], x[i][4 * c + 2], x[i][4 * c + 3]);
+    }
+    __syncwarp();
+    // step 5: u = A x, Delta = ||u - u_prev||
+    float acc1[kPPW][MR];
+    rows_product<MR>(acc1, As, lda, xs, lda, p.Npad, warp, row, hr);
+    ++it;
+#pragma unroll
+    for (int i = 0; i < kPPW; ++i) {
+      float d2 = 0.f;
+#pragma unroll
+      for (int j = 0; j < MR; ++j) {
+        float df = hr[j] ? acc1[i][j] - u[i][j] : 0.f;
+        d2 += df * df;
+        up[i][j] = u[i][j];
+        u[i][j] = acc1[i][j];
+      }
+      d2 = warp_sum(d2);
+      if (!done[i] && d2 < p.eps2) {
+        done[i] = true;
+        write_x<NCH>(p.X, pix0 + i, p.N, x[i], col);
+        if (lane == 0) {
+          if (p.iters_out) p.iters_out[pix0 + i] = it;
+          if (p.conv_out) p.conv_out[pix0 + i] = 1;
+        }
+      }
+    }
+    beta_prev = beta;
+  }
+#pragma unroll
+  for (int i = 0; i < kPPW; ++i) {
+    if (pix0 + i >= p.P) continue;
+    if (!done[i] || p.start_done) {
+      write_x<NCH>(p.X, pix0 + i, p.N, x[i], col);
+      if (lane == 0) {
+        if (p.iters_out) p.iters_out[pix0 + i] = it;
+        if (p.conv_out) p.conv_out[pix0 + i] = 0;
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------
+// Algorithm 2 (ADMM), Woodbury form
+// ---------------------------------------------------------------------------------
+template <int MR, int NCH>
+__global__ void __launch_bounds__(kThreads, 1) k_admm_f32(CvParams p) {
+  extern __shared__ __align__(16) float sm[];
+  const int M = p.M, lda = p.lda, ldw = p.ldw;
+  float* As = sm;
+  float* Ws = As + M * lda;
+  float* xs = Ws + M * ldw;
+  float* es = xs + kT * lda;
+  float* vs = es + kT * ldw;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int64_t pix0 = (int64_t)blockIdx.x * kT + warp * kPPW;
+  const float rho = p.c1, thr = p.c2;
+
+  stage_matrix(As, p.A, M, p.N, lda);
+  stage_matrix(Ws, p.W, M, M, ldw);
+  for (int i = tid; i < kT * lda; i += kThreads) xs[i] = 0.f;
+  for (int i = tid; i < kT * ldw; i += kThreads) es[i] = 0.f;
+
+  int col[NCH], row[MR];
+  bool hc[NCH], hr[MR];
+#pragma unroll
+  for (int c = 0; c < NCH; ++c) {
+    col[c] = 128 * c + 4 * lane;
+    hc[c] = col[c] < p.Npad;
+  }
+#pragma unroll
+  for (int j = 0; j < MR; ++j) {
+    row[j] = lane + 32 * j;
+    hr[j] = row[j] < M;
+  }
+  float yv[kPPW][MR], hp[kPPW][MR];
+  float z[kPPW][4 * NCH], w[kPPW][4 * NCH];
+  bool done[kPPW];
+  bool bad = false;
+#pragma unroll
+  for (int i = 0; i < kPPW; ++i) {
+    bool valid = pix0 + i < p.P;
+    done[i] = !valid || p.start_done;
+#pragma unroll
+    for (int j = 0; j < MR; ++j) {
+      float v = (valid && hr[j]) ? p.Y[(pix0 + i) * M + row[j]] : 0.f;
+      bad |= !isfinite(v);
+      yv[i][j] = v;
+      hp[i][j] = v / rho;  // r^0 = y = rho h^0
+    }
+#pragma unroll
+    for (int k = 0; k < 4 * NCH; ++k) z[i][k] = w[i][k] = 0.f;
+  }
+  if (bad) atomicOr(p.status, kStNonFinite);
+  __syncthreads();
+
+  int it = 0;
+  while (it < p.iters) {
+    if (done[0] && done[1] && done[2] && done[3]) break;  // warp-uniform
+    // d = z - w
+#pragma unroll
+    for (int i = 0; i < kPPW; ++i)
+#pragma unroll
+      for (int c = 0; c < NCH; ++c)
+        if (hc[c])
+          *reinterpret_cast<float4*>(xs + (warp * kPPW + i) * lda + col[c]) =
+              make_float4(z[i][4 * c] - w[i][4 * c], z[i][4 * c + 1] - w[i][4 * c + 1],
+                          z[i][4 * c + 2] - w[i][4 * c + 2], z[i][4 * c + 3] - w[i][4 * c + 3]);
+    __syncwarp();
+    // e = y - A d
+    float acc1[kPPW][MR];
+    rows_product<MR>(acc1, As, lda, xs, lda, p.Npad, warp, row, hr);
+#pragma unroll
+    for (int i = 0; i < kPPW; ++i)
+#pragma unroll
+      for (int j = 0; j < MR; ++j)
+        if (hr[j]) es[(warp * kPPW + i) * ldw + row[j]] = yv[i][j] - acc1[i][j];
+    __syncwarp();
+    // h = W e ; r = rho h ; Delta = rho ||h - h_prev||
+    float h[kPPW][MR];
+    rows_product<MR>(h, Ws, ldw, es, ldw, p.Mpad, warp, row, hr);
+    ++it;
+    bool fin[kPPW], conv[kPPW];
+#pragma unroll
+    for (int i = 0; i < kPPW; ++i) {
+      float d2 = 0.f;
+#pragma unroll
+      for (int j = 0; j < MR; ++j) {
+        float df = hr[j] ? rho * (h[i][j] - hp[i][j]) : 0.f;
+        d2 += df * df;
+        hp[i][j] = h[i][j];
+      }
+      d2 = warp_sum(d2);
+      conv[i] = d2 < p.eps2;
+      fin[i] = !done[i] && (conv[i] || it == p.iters);
+    }
+#pragma unroll
+    for (int j = 0; j < MR; ++j)
+      if (hr[j])
+        *reinterpret_cast<float4*>(vs + row[j] * kLdv + warp * kPPW) =
+            make_float4(h[0][j], h[1][j], h[2][j], h[3][j]);
+    __syncwarp();
+    // x = d + A^T h ; z = soft(x + w, lambda/rho) ; w = w + x - z
+    float acc[kPPW][4 * NCH];
+    cols_product<NCH>(acc, As, lda, vs, M, warp, col, hc);
+#pragma unroll
+    for (int i = 0; i < kPPW; ++i) {
+      if (done[i]) continue;
+      float x[4 * NCH];
+#pragma unroll
+      for (int k = 0; k < 4 * NCH; ++k) {
+        x[k] = (z[i][k] - w[i][k]) + acc[i][k];
+        float zn = soft_thr(x[k] + w[i][k], thr);
+        w[i][k] = w[i][k] + x[k] - zn;
+        z[i][k] = zn;
+      }
+      if (fin[i]) {
+        done[i] = true;
+        write_x<NCH>(p.X, pix0 + i, p.N, x, col);
+        if (lane == 0) {
+          if (p.iters_out) p.iters_out[pix0 + i] = it;
+          if (p.conv_out) p.conv_out[pix0 + i] = conv[i] ? 1 : 0;
+        }
+      }
+    }
+  }
+  // zero iterations (iters == 0 or eps > 1): x = x^0 = 0
+#pragma unroll
+  for (int i = 0; i < kPPW; ++i) {
+    if (pix0 + i >= p.P || it > 0) continue;
+    float x[4 * NCH];
+#pragma unroll
+    for (int k = 0; k < 4 * NCH; ++k) x[k] = 0.f;
+    write_x<NCH>(p.X, pix0 + i, p.N, x, col);
+    if (lane == 0) {
+      if (p.iters_out) p.iters_out[pix0 + i] = 0;
+      if (p.conv_out) p.conv_out[pix0 + i] = 0;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------
+// Eq. 1 measurement: Y = X A^T (+ E), persistent over 32-pixel tiles
+// ---------------------------------------------------------------------------------
+template <int MR>
+__global__ void __launch_bounds__(kThreads, 1) k_measure_f32(CvParams p) {
+  extern __shared__ __align__(16) float sm[];
+  const int M = p.M, N = p.N, lda = p.lda;
+  float* As = sm;
+  float* xs = As + M * lda;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  stage_matrix(As, p.A, M, N, lda);
+  int row[MR];
+  bool hr[MR];
+#pragma unroll
+  for (int j = 0; j < MR; ++j) {
+    row[j] = lane + 32 * j;
+    hr[j] = row[j] < M;
+  }
+  const int64_t ntiles = (p.P + kT - 1) / kT;
+  __syncthreads();
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int64_t pix0 = tile * kT + warp * kPPW;
+    for (int i = 0; i < kPPW; ++i) {
+      bool valid = pix0 + i < p.P;
+      for (int n = lane; n < lda; n += 32)
+        xs[(warp * kPPW + i) * lda + n] = (valid && n < N) ? p.X[(pix0 + i) * N + n] : 0.f;
+    }
+    __syncwarp();
+    float acc[kPPW][MR];
+    rows_product<MR>(acc, As, lda, xs, lda, p.Npad, warp, row, hr);
+    __syncwarp();  // xs is rewritten by the next tile
+#pragma unroll
+    for (int i = 0; i < kPPW; ++i) {
+      if (pix0 + i >= p.P) continue;
+#pragma unroll
+      for (int j = 0; j < MR; ++j) {
+        if (!hr[j]) continue;
+        int64_t o = (pix0 + i) * M + row[j];
+        p.Yout[o] = acc[i][j] + (p.E ? p.E[o] : 0.f);
+      }
+    }
+  }
+}
+
+template <typename K>
+void allow_smem(K kernel, size_t bytes) {
+  cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+CvParams base_params(const Ctx& c) {
+  CvParams p{};
+  p.M = c.M;
+  p.N = c.N;
+  p.Npad = (c.N + 3) & ~3;
+  p.lda = smem_ld(c.N);
+  p.Mpad = (c.M + 3) & ~3;
+  p.ldw = smem_ld(c.M);
+  p.A = c.A32;
+  p.W = c.W32;
+  p.status = c.status;
+  return p;
+}
+
+template <int MR, int NCH>
+cudaError_t fista_mr(const Ctx& c, CvParams p, int64_t blocks) {
+  size_t smem = sizeof(float) * ((size_t)c.M * p.lda + (size_t)kT * p.lda + (size_t)c.M * kLdv);
+  allow_smem(k_fista_f32<MR, NCH>, smem);
+  k_fista_f32<MR, NCH><<<(unsigned)blocks, kThreads, smem, c.stream>>>(p);
+  return cudaGetLastError();
+}
+
+template <int MR, int NCH>
+cudaError_t admm_mr(const Ctx& c, CvParams p, int64_t blocks) {
+  size_t smem = sizeof(float) * ((size_t)c.M * p.lda + (size_t)c.M * p.ldw + (size_t)kT * p.lda +
+                                 (size_t)kT * p.ldw + (size_t)c.M * kLdv);
+  allow_smem(k_admm_f32<MR, NCH>, smem);
+  k_admm_f32<MR, NCH><<<(unsigned)blocks, kThreads, smem, c.stream>>>(p);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+#define CS_DISPATCH_MR_NCH(FN, ...)                                  \
+  do {                                                               \
+    int mr_ = (c.M + 31) / 32, nch_ = (c.N + 127) / 128;             \
+    if (nch_ == 1) {                                                 \
+      if (mr_ == 1) return FN<1, 1>(__VA_ARGS__);                    \
+      if (mr_ == 2) return FN<2, 1>(__VA_ARGS__);                    \
+      if (mr_ == 3) return FN<3, 1>(__VA_ARGS__);                    \
+      return FN<4, 1>(__VA_ARGS__);                                  \
+    } else {                                                         \
+      if (mr_ == 1) return FN<1, 2>(__VA_ARGS__);                    \
+      if (mr_ == 2) return FN<2, 2>(__VA_ARGS__);                    \
+      if (mr_ == 3) return FN<3, 2>(__VA_ARGS__);                    \
+      return FN<4, 2>(__VA_ARGS__);                                  \
+    }                                                                \
+  } while (0)
+
+cudaError_t launch_fista(const Ctx& c, const ConvexArgs& a) {
+  CvParams p = base_params(c);
+  p.Y = a.Y;
+  p.X = a.X;
+  p.P = a.P;
+  p.c1 = (float)(1.0 / c.L);
+  p.c2 = (float)(a.lambda / c.L);
+  p.eps2 = (float)(a.eps * a.eps);
+  p.start_done = a.eps > 1.0;
+  p.iters = a.iters;
+  p.iters_out = a.iters_out;
+  p.conv_out = a.conv_out;
+  int64_t blocks = (a.P + kT - 1) / kT;
+  if (blocks == 0) return cudaSuccess;
+  CS_DISPATCH_MR_NCH(fista_mr, c, p, blocks);
+}
+
+cudaError_t launch_admm(const Ctx& c, const ConvexArgs& a) {
+  CvParams p = base_params(c);
+  p.Y = a.Y;
+  p.X = a.X;
+  p.P = a.P;
+  p.c1 = (float)a.rho;
+  p.c2 = (float)(a.lambda / a.rho);
+  p.eps2 = (float)(a.eps * a.eps);
+  p.start_done = a.eps > 1.0;
+  p.iters = a.iters;
+  p.iters_out = a.iters_out;
+  p.conv_out = a.conv_out;
+  int64_t blocks = (a.P + kT - 1) / kT;
+  if (blocks == 0) return cudaSuccess;
+  CS_DISPATCH_MR_NCH(admm_mr, c, p, blocks);
+}
+
+template <int MR>
+static cudaError_t measure_mr(const Ctx& c, CvParams p) {
+  size_t smem = sizeof(float) * ((size_t)c.M * p.lda + (size_t)kT * p.lda);
+  allow_smem(k_measure_f32<MR>, smem);
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_measure_f32<MR>, kThreads, smem);
+  int64_t ntiles = (p.P + kT - 1) / kT;
+  int64_t grid = (int64_t)c.num_sms * (per_sm > 0 ? per_sm : 1);
+  if (grid > ntiles) grid = ntiles;
+  k_measure_f32<MR><<<(unsigned)grid, kThreads, smem, c.stream>>>(p);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_measure(const Ctx& c, const float* X, float* Y, const float* E, int64_t P) {
+  CvParams p = base_params(c);
+  p.Yout = Y;
+  p.X = const_cast<float*>(X);
+  p.E = E;
+  p.P = P;
+  if (P == 0) return cudaSuccess;
+  int mr = (c.M + 31) / 32;
+  if (mr == 1) return measure_mr<1>(c, p);
+  if (mr == 2) return measure_mr<2>(c, p);
+  if (mr == 3) return measure_mr<3>(c, p);
+  return measure_mr<4>(c, p);
+}
+
+}  // namespace cs

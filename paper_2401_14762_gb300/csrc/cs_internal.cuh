@@ -1,0 +1,111 @@
+// Internal declarations shared by the translation units of libcs_hsi.so.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "cs_hsi.h"
+
+namespace cs {
+
+// Bits of the per-context device status word (atomicOr'ed by kernels).
+enum : int {
+  kStNonFinite = 1 << 0,
+  kStNotSpd = 1 << 1,
+  kStTimeout = 1 << 2,
+};
+
+constexpr int kMaxM = 128;
+constexpr int kMaxN = 256;
+
+// Padded leading dimension (in floats) for a row of `n` floats kept in shared memory:
+// at least n rounded up to 4, and == 4 (mod 8) so that eight lanes reading float4s
+// from eight consecutive rows at the same column hit 32 distinct banks.
+inline int smem_ld(int n) {
+  int ld = (n + 3) & ~3;
+  while ((ld & 7) != 4) ld += 4;
+  return ld;
+}
+
+struct Ctx {
+  int M = 0, N = 0, device = 0, num_sms = 0;
+  cudaStream_t stream = nullptr;
+  double L = 0.0;             // Lipschitz constant lambda_max(A^T A)
+  double* A64 = nullptr;      // M x N, FP64
+  double* At64 = nullptr;     // N x M, FP64 (column j of A contiguous)
+  double* G64 = nullptr;      // N x N, FP64 Gram A^T A
+  float* A32 = nullptr;       // M x N, FP32
+  float* At32 = nullptr;      // N x M, FP32
+  double rho = 0.0;           // penalty of the cached ADMM factor
+  float* W32 = nullptr;       // M x M, FP32 (A A^T + rho I)^{-1}
+  double* scratch64 = nullptr;  // setup scratch
+  size_t scratch_elems = 0;
+  int* status = nullptr;      // device status word
+  int* counter = nullptr;     // work counter of the persistent greedy kernel
+  float* stage_in = nullptr;  // staging for host-pointer calls
+  float* stage_out = nullptr;
+  float* stage_aux = nullptr;
+  size_t stage_in_bytes = 0, stage_out_bytes = 0, stage_aux_bytes = 0;
+};
+
+void set_error(const std::string& msg);
+cs_status cuda_fail(cudaError_t e, const char* what);
+
+// ---- setup (FP64, one-off) ----
+cudaError_t setup_dictionary(Ctx& c, const double* A_host, const double* Phi_host,
+                             const double* Psi_host);
+cudaError_t setup_admm_factor(Ctx& c, double rho);
+
+// ---- measurement ----
+cudaError_t launch_measure(const Ctx& c, const float* X, float* Y, const float* E, int64_t P);
+
+// ---- convex (FISTA / ADMM) ----
+struct ConvexArgs {
+  const float* Y;
+  float* X;
+  int64_t P;
+  double lambda;
+  double rho;
+  double eps;
+  int iters;
+  int32_t* iters_out;
+  uint8_t* conv_out;
+  cs_precision prec;
+};
+cudaError_t launch_fista(const Ctx& c, const ConvexArgs& a);
+cudaError_t launch_admm(const Ctx& c, const ConvexArgs& a);
+
+// ---- greedy (gOMP / BIHT / CoSaMP) ----
+enum GreedyAlgo { kGomp = 0, kBiht = 1, kCosamp = 2 };
+struct GreedyArgs {
+  const float* Y;
+  float* X;
+  int64_t P;
+  int kappa;
+  int G;  // gOMP atoms per iteration (0 = per-pixel rule from kappa_pp)
+  double mu;
+  double eps;
+  int max_iters;
+  const int16_t* kappa_pp;
+  int kappa_max;  // upper bound of kappa over all pixels
+  int32_t* iters_out;
+  uint8_t* conv_out;
+  cs_precision prec;
+};
+cudaError_t launch_greedy(const Ctx& c, GreedyAlgo algo, const GreedyArgs& a);
+
+// ---- warp helpers ----
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+}  // namespace cs

@@ -1,0 +1,625 @@
+// Greedy recovery: gOMP (Algorithm 3), BIHT (Algorithm 4) and CoSaMP (Algorithm 5).
+//
+// One warp recovers one pixel at a time and takes the next pixel from a global work
+// counter when it finishes, so pixels that stop early (Delta < eps) free their warp at
+// once.  Per iteration the warp
+//   1. correlates: p = A^T r (FP32, lane l owns atoms l, l+32, ...), for BIHT
+//      u = x + mu p,
+//   2. selects the G / 2 kappa / kappa largest magnitudes with warp argmax rounds
+//      (ties to the lower atom index),
+//   3. forms the support c (union of Theta with c or supp(x)),
+//   4. solves min ||A_c s - y|| through the normal equations G_c s = (A^T y)_c in FP64:
+//      G_c comes from the precomputed FP64 Gram matrix A^T A and is factored row by
+//      row (G_c = L L^T, the next row from a forward substitution), so gOMP, whose
+//      support only grows, extends its factor instead of refactoring; when |c| > M the
+//      minimum-norm solution s = A_c^T (A_c A_c^T)^{-1} y is used instead,
+//   5. prunes to kappa atoms (and, for gOMP, refits on them),
+//   6. recomputes the residual r = y - A x and Delta = ||r - r_prev|| in FP64 (the
+//      paper's absolute eps = 1e-8 lies below FP32 resolution of r).
+// Supports are kept sorted by atom index (gOMP's growing c in insertion order), so an
+// unchanged support reproduces x bit for bit and Delta = 0 exactly, as in the paper's
+// stopping rule.  All per-pixel state sits in the warp's slice of shared memory.
+#include <cuda_runtime.h>
+
+#include "cs_internal.cuh"
+
+namespace cs {
+namespace {
+
+constexpr int kNK = kMaxN / 32;  // atoms per lane
+
+struct GrParams {
+  int M, N, algo;
+  const float* A32;    // M x N
+  const float* At32;   // N x M
+  const double* At64;  // N x M
+  const double* G64;   // N x N
+  const float* Y;
+  float* X;
+  int64_t P;
+  int kappa, G;
+  const int16_t* kappa_pp;
+  float mu;
+  double eps2;
+  int start_done;
+  int max_iters;
+  int cmax, dmax, kmax;
+  int warp_bytes;
+  int32_t* iters_out;
+  uint8_t* conv_out;
+  int* status;
+  unsigned long long* counter;
+};
+
+// Byte offsets of one warp's shared-memory slice.
+struct Layout {
+  int y, r, xd, b, bflag, inc, c, q, sel, tmp16, xq, L, invd, v, s, wv, Lq, invq, vq, sq,
+      svals, total;
+  __host__ __device__ Layout(int M, int N, int cmax, int dmax, int kmax) {
+    int o = 0;
+    auto take = [&](int bytes, int align) {
+      o = (o + align - 1) / align * align;
+      int at = o;
+      o += bytes;
+      return at;
+    };
+    b = take(8 * N, 8);
+    xq = take(8 * kmax, 8);
+    L = take(8 * (dmax * (dmax + 1) / 2), 8);
+    invd = take(8 * dmax, 8);
+    v = take(8 * dmax, 8);
+    s = take(8 * cmax, 8);
+    wv = take(8 * N, 8);
+    Lq = take(8 * (kmax * (kmax + 1) / 2), 8);
+    invq = take(8 * kmax, 8);
+    vq = take(8 * kmax, 8);
+    sq = take(8 * kmax, 8);
+    svals = take(8 * cmax, 8);
+    r = take(8 * M, 8);
+    y = take(4 * M, 4);
+    xd = take(4 * N, 4);
+    c = take(2 * cmax, 2);
+    q = take(2 * kmax, 2);
+    sel = take(2 * N, 2);
+    tmp16 = take(2 * N, 2);
+    bflag = take(N, 1);
+    inc = take(N, 1);
+    total = (o + 15) / 16 * 16;
+  }
+};
+
+// Column-major packed lower-triangular storage with column capacity `cap`:
+// entry (t, i), t >= i, lives at i*cap - i*(i+1)/2 + t.
+__device__ __forceinline__ int lidx(int t, int i, int cap) { return i * cap - i * (i + 1) / 2 + t; }
+
+struct Warp {
+  const GrParams& p;
+  int lane;
+  float *y, *xd;
+  double *r, *b, *xq, *L, *invd, *v, *s, *wv, *Lq, *invq, *vq, *sq, *svals;
+  uint8_t *bflag, *inc;
+  int16_t *c, *q, *sel, *tmp16;
+};
+
+// (A^T y)_j in FP64, computed once per pixel and atom.
+__device__ double rhs(Warp& w, int j) {
+  if (!w.bflag[j]) {  // warp-uniform
+    const double* a = w.p.At64 + (size_t)j * w.p.M;
+    double part = 0.0;
+    for (int m = w.lane; m < w.p.M; m += 32) part += a[m] * (double)w.y[m];
+    part = warp_sum(part);
+    __syncwarp();
+    if (w.lane == 0) {
+      w.b[j] = part;
+      w.bflag[j] = 1;
+    }
+    __syncwarp();
+    return part;
+  }
+  return w.b[j];
+}
+
+// Appends row n to the factor L of a growing normal-equation system.  g(t) gives the
+// system entry (n, t) for t <= n.  Forward substitution L_{0:n} w = g(0:n) by columns,
+// then l_nn = sqrt(g(n,n) - w.w).  Also extends v = L^{-1} rhs with rhs_n.
+// Returns false if the pivot is not positive (system not numerically definite).
+template <typename GF>
+__device__ bool append_row(Warp& w, double* L, double* invd, double* v, int cap, int n, GF g,
+                           double rhs_n) {
+  const int lane = w.lane;
+  double* wv = w.wv;
+  for (int t = lane; t < n; t += 32) wv[t] = g(t);
+  double gnn = g(n);
+  __syncwarp();
+  for (int i = 0; i < n; ++i) {
+    double wi = wv[i] * invd[i];
+    __syncwarp();
+    if (lane == 0) wv[i] = wi;
+    const double* col = L + lidx(0, i, cap);
+    for (int t = i + 1 + lane; t < n; t += 32) wv[t] -= col[t] * wi;
+    __syncwarp();
+  }
+  double ww = 0.0, wvv = 0.0;
+  for (int t = lane; t < n; t += 32) {
+    ww += wv[t] * wv[t];
+    wvv += wv[t] * v[t];
+    L[lidx(n, t, cap)] = wv[t];
+  }
+  ww = warp_sum(ww);
+  wvv = warp_sum(wvv);
+  double d = gnn - ww;
+  bool ok = d > 1e-13 * fabs(gnn) && isfinite(d);
+  double lnn = sqrt(ok ? d : 1.0);
+  __syncwarp();
+  if (lane == 0) {
+    L[lidx(n, n, cap)] = lnn;
+    invd[n] = 1.0 / lnn;
+    v[n] = (rhs_n - wvv) / lnn;
+  }
+  __syncwarp();
+  return ok;
+}
+
+// Solves L^T s = v (n x n) by rows, right-looking.
+__device__ void back_solve(Warp& w, const double* L, const double* invd, const double* v,
+                           double* s, int cap, int n) {
+  const int lane = w.lane;
+  for (int t = lane; t < n; t += 32) s[t] = v[t];
+  __syncwarp();
+  for (int i = n - 1; i >= 0; --i) {
+    double si = s[i] * invd[i];
+    __syncwarp();
+    if (lane == 0) s[i] = si;
+    for (int t = lane; t < i; t += 32) s[t] -= L[lidx(i, t, cap)] * si;
+    __syncwarp();
+  }
+}
+
+// k rounds of warp argmax over the lane-held values val[kk] (atom lane + 32 kk, only
+// atoms < nvalid compete): largest |val| first, ties to the lower atom.  Writes the
+// chosen atoms to out[0..k).
+__device__ void topk_atoms(Warp& w, const float (&val)[kNK], int nvalid, int k, int16_t* out) {
+  unsigned taken = 0;
+  for (int j = 0; j < k; ++j) {
+    float bv = -1.f;
+    int bn = 1 << 30;
+#pragma unroll
+    for (int kk = 0; kk < kNK; ++kk) {
+      int n = w.lane + 32 * kk;
+      if (n < nvalid && !((taken >> kk) & 1u)) {
+        float a = fabsf(val[kk]);
+        if (a > bv || (a == bv && n < bn)) {
+          bv = a;
+          bn = n;
+        }
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      float ov = __shfl_xor_sync(0xffffffffu, bv, o);
+      int on = __shfl_xor_sync(0xffffffffu, bn, o);
+      if (ov > bv || (ov == bv && on < bn)) {
+        bv = ov;
+        bn = on;
+      }
+    }
+    if ((bn & 31) == w.lane) taken |= 1u << (bn >> 5);
+    if (w.lane == 0) out[j] = (int16_t)bn;
+  }
+  __syncwarp();
+}
+
+// k rounds of warp argmax over FP64 values vals[0..cnt) keyed by atoms[0..cnt):
+// largest |value| first, ties to the lower atom.  Writes chosen positions to out.
+__device__ void topk_positions(Warp& w, const double* vals, const int16_t* atoms, int cnt, int k,
+                               int16_t* out) {
+  constexpr int kPK = kMaxN / 32;
+  double lv[kPK];
+  int la[kPK];
+#pragma unroll
+  for (int kk = 0; kk < kPK; ++kk) {
+    int j = w.lane + 32 * kk;
+    lv[kk] = j < cnt ? fabs(vals[j]) : -1.0;
+    la[kk] = j < cnt ? atoms[j] : (1 << 30);
+  }
+  unsigned taken = 0;
+  for (int j = 0; j < k; ++j) {
+    double bv = -2.0;
+    int ba = 1 << 30, bp = -1;
+#pragma unroll
+    for (int kk = 0; kk < kPK; ++kk) {
+      int pos = w.lane + 32 * kk;
+      if (pos < cnt && !((taken >> kk) & 1u)) {
+        if (lv[kk] > bv || (lv[kk] == bv && la[kk] < ba)) {
+          bv = lv[kk];
+          ba = la[kk];
+          bp = pos;
+        }
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      double ov = __shfl_xor_sync(0xffffffffu, bv, o);
+      int oa = __shfl_xor_sync(0xffffffffu, ba, o);
+      int op = __shfl_xor_sync(0xffffffffu, bp, o);
+      if (ov > bv || (ov == bv && oa < ba)) {
+        bv = ov;
+        ba = oa;
+        bp = op;
+      }
+    }
+    if ((bp & 31) == w.lane) taken |= 1u << (bp >> 5);
+    if (w.lane == 0) out[j] = (int16_t)bp;
+  }
+  __syncwarp();
+}
+
+// Sorts atoms[0..n) ascending (distinct keys) by rank, carrying FP64 values if given.
+__device__ void sort_atoms(Warp& w, int16_t* atoms, double* vals, int n) {
+  int16_t* tmp = w.tmp16;
+  double* tv = w.wv;
+  for (int j = w.lane; j < n; j += 32) {
+    int a = atoms[j], rank = 0;
+    for (int t = 0; t < n; ++t) rank += atoms[t] < a;
+    tmp[rank] = (int16_t)a;
+    if (vals) tv[rank] = vals[j];
+  }
+  __syncwarp();
+  for (int j = w.lane; j < n; j += 32) {
+    atoms[j] = tmp[j];
+    if (vals) vals[j] = tv[j];
+  }
+  __syncwarp();
+}
+
+// Fresh factorisation of the normal equations on atoms[0..n) and solve into s.
+__device__ bool ls_fresh(Warp& w, const int16_t* atoms, int n, double* L, double* invd, double* v,
+                         double* s, int cap) {
+  const double* G = w.p.G64;
+  const int N = w.p.N;
+  bool ok = true;
+  for (int k = 0; k < n; ++k) {
+    const double* grow = G + (size_t)atoms[k] * N;
+    double bk = rhs(w, atoms[k]);
+    ok &= append_row(w, L, invd, v, cap, k, [&](int t) { return grow[atoms[t]]; }, bk);
+    if (!ok) return false;
+  }
+  back_solve(w, L, invd, v, s, cap, n);
+  return true;
+}
+
+// Minimum-norm solution for |c| > M: s = A_c^T H^{-1} y with H = A_c A_c^T (M x M).
+__device__ bool ls_min_norm(Warp& w, const int16_t* atoms, int n, double* s) {
+  const int M = w.p.M;
+  const double* At = w.p.At64;
+  double* L = w.L;
+  const int cap = M;
+  bool ok = true;
+  for (int k = 0; k < M; ++k) {
+    // row k of H: H(k, t) = sum_j A[k][c_j] A[t][c_j]
+    ok &= append_row(
+        w, L, w.invd, w.v, cap, k,
+        [&](int t) {
+          double h = 0.0;
+          for (int j = 0; j < n; ++j) {
+            const double* a = At + (size_t)atoms[j] * M;
+            h += a[k] * a[t];
+          }
+          return h;
+        },
+        (double)w.y[k]);
+    if (!ok) return false;
+  }
+  double* zv = w.svals;  // z = H^{-1} y
+  back_solve(w, L, w.invd, w.v, zv, cap, M);
+  for (int j = w.lane; j < n; j += 32) {
+    const double* a = At + (size_t)atoms[j] * M;
+    double acc = 0.0;
+    for (int m = 0; m < M; ++m) acc += a[m] * zv[m];
+    s[j] = acc;
+  }
+  __syncwarp();
+  return true;
+}
+
+template <int ALGO>
+__global__ void __launch_bounds__(256) k_greedy(GrParams p) {
+  extern __shared__ __align__(16) unsigned char gsm[];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int M = p.M, N = p.N;
+  Layout lay(M, N, p.cmax, p.dmax, p.kmax);
+  unsigned char* base = gsm + (size_t)wid * p.warp_bytes;
+  Warp w{p, lane};
+  w.y = (float*)(base + lay.y);
+  w.r = (double*)(base + lay.r);
+  w.xd = (float*)(base + lay.xd);
+  w.b = (double*)(base + lay.b);
+  w.xq = (double*)(base + lay.xq);
+  w.L = (double*)(base + lay.L);
+  w.invd = (double*)(base + lay.invd);
+  w.v = (double*)(base + lay.v);
+  w.s = (double*)(base + lay.s);
+  w.wv = (double*)(base + lay.wv);
+  w.Lq = (double*)(base + lay.Lq);
+  w.invq = (double*)(base + lay.invq);
+  w.vq = (double*)(base + lay.vq);
+  w.sq = (double*)(base + lay.sq);
+  w.svals = (double*)(base + lay.svals);
+  w.bflag = base + lay.bflag;
+  w.inc = base + lay.inc;
+  w.c = (int16_t*)(base + lay.c);
+  w.q = (int16_t*)(base + lay.q);
+  w.sel = (int16_t*)(base + lay.sel);
+  w.tmp16 = (int16_t*)(base + lay.tmp16);
+
+  for (int n = lane; n < N; n += 32) {
+    w.xd[n] = 0.f;
+    w.bflag[n] = 0;
+    w.inc[n] = 0;
+  }
+  __syncwarp();
+
+  for (;;) {
+    unsigned long long pix_u = 0;
+    if (lane == 0) pix_u = atomicAdd(p.counter, 1ull);
+    pix_u = __shfl_sync(0xffffffffu, pix_u, 0);
+    if (pix_u >= (unsigned long long)p.P) break;
+    const int64_t pix = (int64_t)pix_u;
+
+    const int kappa = p.kappa_pp ? (int)p.kappa_pp[pix] : p.kappa;
+    const int G = p.G > 0 ? p.G : (kappa / 5 > 1 ? kappa / 5 : 1);
+    int cap = p.max_iters;
+    if (ALGO == kGomp) {
+      if (kappa < cap) cap = kappa;
+      if (M / G < cap) cap = M / G;
+    }
+    bool bad = false;
+    for (int m = lane; m < M; m += 32) {
+      float yv = p.Y[pix * M + m];
+      bad |= !isfinite(yv);
+      w.y[m] = yv;
+      w.r[m] = (double)yv;  // r^0 = y
+    }
+    if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(p.status, kStNonFinite);
+    __syncwarp();
+
+    int nc = 0, nq = 0, it = 0;
+    uint8_t conv = 0;
+    bool fail = false;
+    while (!p.start_done && it < cap) {
+      // ---- step 1: correlation (u = x + mu p for BIHT) ----
+      float val[kNK];
+#pragma unroll
+      for (int kk = 0; kk < kNK; ++kk) val[kk] = 0.f;
+      for (int m = 0; m < M; ++m) {
+        float rm = (float)w.r[m];
+        const float* arow = p.A32 + (size_t)m * N;
+#pragma unroll
+        for (int kk = 0; kk < kNK; ++kk) {
+          int n = lane + 32 * kk;
+          if (n < N) val[kk] += arow[n] * rm;
+        }
+      }
+      if (ALGO == kBiht) {
+#pragma unroll
+        for (int kk = 0; kk < kNK; ++kk) {
+          int n = lane + 32 * kk;
+          if (n < N) val[kk] = w.xd[n] + p.mu * val[kk];
+        }
+      }
+      const int ksel = ALGO == kGomp ? G : (ALGO == kCosamp ? 2 * kappa : kappa);
+      topk_atoms(w, val, N, ksel, w.sel);
+
+      // ---- support c ----
+      int nc_old = nc;
+      if (ALGO == kGomp) {
+        // c = Theta U c, new atoms appended in selection order
+        for (int j = 0; j < ksel; ++j) {
+          int a = w.sel[j];
+          if (!w.inc[a]) {
+            __syncwarp();
+            if (lane == 0) {
+              w.inc[a] = 1;
+              w.c[nc] = (int16_t)a;
+            }
+            ++nc;
+          }
+          __syncwarp();
+        }
+      } else {
+        // CoSaMP: c = Theta U c_prev (c_prev = last pruned support);
+        // BIHT: c = Theta U supp(x).  Both held sorted.
+        if (ALGO == kBiht) {
+          nc = 0;
+          for (int j = 0; j < nq; ++j)
+            if (w.xq[j] != 0.0) {
+              if (lane == 0) w.c[nc] = w.q[j];
+              ++nc;
+            }
+          __syncwarp();
+          for (int n = lane; n < N; n += 32) w.inc[n] = 0;
+          __syncwarp();
+          for (int j = lane; j < nc; j += 32) w.inc[w.c[j]] = 1;
+          __syncwarp();
+        }
+        for (int j = 0; j < ksel; ++j) {
+          int a = w.sel[j];
+          if (!w.inc[a]) {
+            __syncwarp();
+            if (lane == 0) {
+              w.inc[a] = 1;
+              w.c[nc] = (int16_t)a;
+            }
+            ++nc;
+          }
+          __syncwarp();
+        }
+        sort_atoms(w, w.c, nullptr, nc);
+      }
+
+      // ---- step 2: least squares on c ----
+      if (nc > 0) {
+        if (ALGO == kGomp) {
+          const double* G64 = p.G64;
+          for (int k = nc_old; k < nc && !fail; ++k) {
+            const double* grow = G64 + (size_t)w.c[k] * N;
+            double bk = rhs(w, w.c[k]);
+            const int16_t* cc = w.c;
+            fail |= !append_row(w, w.L, w.invd, w.v, p.dmax, k, [&](int t) { return grow[cc[t]]; },
+                                bk);
+          }
+          if (!fail) back_solve(w, w.L, w.invd, w.v, w.s, p.dmax, nc);
+        } else if (nc <= M) {
+          fail |= !ls_fresh(w, w.c, nc, w.L, w.invd, w.v, w.s, p.dmax);
+        } else {
+          fail |= !ls_min_norm(w, w.c, nc, w.s);
+        }
+      }
+      if (fail) break;
+
+      // ---- step 3: prune to kappa (and refit for gOMP) ----
+      // previous support leaves xd
+      for (int j = lane; j < nq; j += 32) w.xd[w.q[j]] = 0.f;
+      __syncwarp();
+      int keep = nc < kappa ? nc : kappa;
+      if (nc > kappa) {
+        topk_positions(w, w.s, w.c, nc, keep, w.sel);
+      } else {
+        for (int j = lane; j < nc; j += 32) w.sel[j] = (int16_t)j;
+        __syncwarp();
+      }
+      for (int j = lane; j < keep; j += 32) {
+        int pos = w.sel[j];
+        w.q[j] = w.c[pos];
+        w.xq[j] = w.s[pos];
+      }
+      __syncwarp();
+      nq = keep;
+      sort_atoms(w, w.q, w.xq, nq);
+      if (ALGO == kGomp && nq > 0) {
+        fail |= !ls_fresh(w, w.q, nq, w.Lq, w.invq, w.vq, w.sq, p.kmax);
+        if (fail) break;
+        for (int j = lane; j < nq; j += 32) w.xq[j] = w.sq[j];
+        __syncwarp();
+      }
+      if (ALGO == kCosamp) {
+        // c = c(q)
+        for (int j = lane; j < nc; j += 32) w.inc[w.c[j]] = 0;
+        __syncwarp();
+        for (int j = lane; j < nq; j += 32) {
+          w.c[j] = w.q[j];
+          w.inc[w.q[j]] = 1;
+        }
+        __syncwarp();
+        nc = nq;
+      }
+      for (int j = lane; j < nq; j += 32) w.xd[w.q[j]] = (float)w.xq[j];
+      __syncwarp();
+
+      // ---- step 4: r = y - A x, Delta (FP64) ----
+      double d2 = 0.0;
+      for (int m = lane; m < M; m += 32) {
+        double acc = 0.0;
+        for (int j = 0; j < nq; ++j) acc += p.At64[(size_t)w.q[j] * M + m] * w.xq[j];
+        double rn = (double)w.y[m] - acc;
+        double df = rn - w.r[m];
+        d2 += df * df;
+        w.r[m] = rn;
+      }
+      d2 = warp_sum(d2);
+      __syncwarp();
+      ++it;
+      if (d2 < p.eps2) {
+        conv = 1;
+        break;
+      }
+    }
+    if (fail) {
+      conv = 2;
+      if (lane == 0) atomicOr(p.status, kStNotSpd);
+    }
+    // output and reset
+    for (int n = lane; n < N; n += 32) {
+      p.X[pix * N + n] = w.xd[n];
+      w.xd[n] = 0.f;
+      w.bflag[n] = 0;
+      w.inc[n] = 0;
+    }
+    if (lane == 0) {
+      if (p.iters_out) p.iters_out[pix] = it;
+      if (p.conv_out) p.conv_out[pix] = conv;
+    }
+    __syncwarp();
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_greedy(const Ctx& c, GreedyAlgo algo, const GreedyArgs& a) {
+  if (a.P == 0) return cudaSuccess;
+  GrParams p{};
+  p.M = c.M;
+  p.N = c.N;
+  p.algo = algo;
+  p.A32 = c.A32;
+  p.At32 = c.At32;
+  p.At64 = c.At64;
+  p.G64 = c.G64;
+  p.Y = a.Y;
+  p.X = a.X;
+  p.P = a.P;
+  p.kappa = a.kappa;
+  p.G = a.G;
+  p.kappa_pp = a.kappa_pp;
+  p.mu = (float)a.mu;
+  p.eps2 = a.eps * a.eps;
+  p.start_done = a.eps > 1.0;
+  p.max_iters = a.max_iters;
+  p.iters_out = a.iters_out;
+  p.conv_out = a.conv_out;
+  p.status = c.status;
+  p.counter = reinterpret_cast<unsigned long long*>(c.counter);
+  const int K = a.kappa_max;
+  const int M = c.M, N = c.N;
+  int cmax;
+  if (algo == kGomp) {
+    int gmax = a.G > 0 ? a.G : (K / 5 > 1 ? K / 5 : 1);
+    int iters = a.max_iters < K ? a.max_iters : K;
+    long long cm = (long long)gmax * (iters > 0 ? iters : 1);
+    cmax = (int)(cm < M ? cm : M);
+    if (a.G == 0) cmax = M;  // per-pixel G: bound by M
+  } else if (algo == kCosamp) {
+    cmax = 3 * K < N ? 3 * K : N;
+  } else {
+    cmax = 2 * K < N ? 2 * K : N;
+  }
+  if (cmax < 1) cmax = 1;
+  p.cmax = cmax;
+  p.dmax = cmax < M ? cmax : M;
+  p.kmax = K > 0 ? K : 1;
+  Layout lay(M, N, p.cmax, p.dmax, p.kmax);
+  p.warp_bytes = lay.total;
+  const int max_smem = 220 * 1024;
+  int warps = max_smem / lay.total;
+  if (warps > 8) warps = 8;
+  if (warps < 1) return cudaErrorInvalidConfiguration;
+  size_t smem = (size_t)warps * lay.total;
+  cudaError_t e = cudaMemsetAsync(c.counter, 0, sizeof(unsigned long long), c.stream);
+  if (e != cudaSuccess) return e;
+  auto launch = [&](auto kern) {
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, warps * 32, smem);
+    if (per_sm < 1) per_sm = 1;
+    long long grid = (long long)c.num_sms * per_sm;
+    long long need = (a.P + warps - 1) / warps;
+    if (grid > need) grid = need;
+    kern<<<(unsigned)grid, warps * 32, smem, c.stream>>>(p);
+    return cudaGetLastError();
+  };
+  if (algo == kGomp) return launch(k_greedy<kGomp>);
+  if (algo == kBiht) return launch(k_greedy<kBiht>);
+  return launch(k_greedy<kCosamp>);
+}
+
+}  // namespace cs

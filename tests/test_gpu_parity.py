@@ -1,0 +1,314 @@
+"""CUDA path (through the C ABI) against the FP64 oracle on identical seeded inputs.
+
+Sizes span several 32-pixel tiles with a ragged tail; dimensions follow the small
+(N=120, M=48) and FP32 (N=200, M=80) cube recipes.  Tolerances: relative L2 <= 1e-5
+for the FP32 path; greedy supports identical on well-separated pixels.
+"""
+import numpy as np
+import pytest
+
+import oracle as orc
+from gpu_common import (MARGIN_FP32, REL_L2_FP32, Problem, fixed_iteration_tolerance,
+                        gpu_run, iterate_conditioning, library, rel_l2, support, support_check)
+from oracle_pins import rand_orthogonal, soft_np
+from paper_2401_14762_gb300 import synthetic as sy
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def cs():
+    return library()
+
+
+@pytest.fixture(scope="module")
+def small():
+    return Problem(48, 120, 32 * 32 + 7, "sparse", seed=1, S=8)
+
+
+@pytest.fixture(scope="module")
+def plaw():
+    return Problem(80, 200, 32 * 9 + 5, "powerlaw", seed=2, noise_var=1e-3)
+
+
+# --------------------------------------------------------------------------- setup
+@pytest.mark.parametrize("M,N,seed", [(48, 120, 1), (80, 200, 2), (90, 224, 3), (102, 256, 4),
+                                      (5, 7, 5), (64, 64, 6)])
+def test_setup_dictionary_lipschitz(cs, M, N, seed):
+    Phi = sy.gaussian_phi(M, N, seed)
+    A = orc.dictionary(Phi)
+    ctx = cs.cs_create(M, N, Phi=Phi)
+    assert np.abs(cs.cs_get_dictionary(ctx) - A).max() < 1e-13
+    L = orc.lipschitz(A)
+    assert abs(cs.cs_get_lipschitz(ctx) - L) <= 1e-12 * L
+
+
+def test_setup_given_A_and_Psi(cs):
+    M, N = 20, 32
+    Phi = sy.gaussian_phi(M, N, 7)
+    Psi = rand_orthogonal(N, 8)
+    ctx = cs.cs_create(M, N, Phi=Phi, Psi=Psi)
+    assert np.abs(cs.cs_get_dictionary(ctx) - orc.dictionary(Phi, Psi)).max() < 1e-13
+    A = orc.dictionary(Phi)
+    ctx2 = cs.cs_create(M, N, A=A)
+    assert np.abs(cs.cs_get_dictionary(ctx2) - A).max() == 0.0
+
+
+# --------------------------------------------------------------------------- measure
+@pytest.mark.parametrize("M,N", [(48, 120), (80, 200), (102, 256), (3, 5)])
+def test_measure(cs, M, N):
+    torch = pytest.importorskip("torch")
+    P = 32 * 5 + 3
+    Phi = sy.gaussian_phi(M, N, 3)
+    A = orc.dictionary(Phi)
+    X = sy.powerlaw_coeffs(P, N, 3, permute=True).astype(np.float32)
+    E = sy.noise(P, M, 1e-3, 3).astype(np.float32)
+    ctx = cs.cs_create(M, N, Phi=Phi)
+    Yd = torch.zeros((P, M), device="cuda")
+    cs.cs_measure(ctx, torch.from_numpy(X).cuda(), Yd, torch.from_numpy(E).cuda())
+    cs.cs_sync(ctx)
+    ref = orc.measure(A, X.astype(np.float64), E.astype(np.float64))
+    scale = np.linalg.norm(ref, axis=1, keepdims=True)
+    assert (np.abs(Yd.cpu().numpy() - ref) / scale).max() < 1e-6
+
+
+# --------------------------------------------------------------------------- FISTA
+def _fista_fixed(cs, pr, lam, iters):
+    """A fixed, unconverged iteration count: the oracle's own output is ill-conditioned
+    there (momentum amplifies perturbations in weakly determined directions), so the
+    FP32 tolerance follows from its measured conditioning."""
+    run = lambda Y: orc.fista(pr.A, Y, pr.L, lam, 0.0, iters)[0]
+    Xo = run(pr.Y)
+    tol = fixed_iteration_tolerance(iterate_conditioning(run, pr.Y[:128]), iters)
+    ctx = cs.cs_create(pr.M, pr.N, Phi=pr.Phi)
+    Xg, it, cv = gpu_run(cs.cs_recover_fista, ctx, pr.Y, pr.N, lam, iters, eps=0.0)
+    assert rel_l2(Xg, Xo) <= tol, (rel_l2(Xg, Xo), tol)
+    assert np.all(it == iters) and np.all(cv == 0)
+
+
+def test_fista_small(cs, small):
+    _fista_fixed(cs, small, 1e-3, 500)
+
+
+def test_fista_powerlaw(cs, plaw):
+    _fista_fixed(cs, plaw, 1e-3, 300)
+
+
+@pytest.mark.parametrize("lam", [0.05, 0.02])
+def test_fista_converged(cs, lam):
+    """Run to the LASSO solution (Delta < eps): the map is contractive there and the FP32
+    path meets the 1e-5 bound."""
+    pr = Problem(48, 120, 200, "sparse", seed=21, S=6, noise_var=1e-4)
+    Xo, _ = orc.fista(pr.A, pr.Y, pr.L, lam, 0.0, 20000)
+    ctx = cs.cs_create(pr.M, pr.N, Phi=pr.Phi)
+    Xg, it, cv = gpu_run(cs.cs_recover_fista, ctx, pr.Y, pr.N, lam, 20000, eps=1e-7)
+    assert rel_l2(Xg, Xo) <= REL_L2_FP32
+    assert np.all(support(Xg) == support(Xo))
+
+
+def test_fista_delta_stop(cs):
+    """A orthogonal: x^2 = x^1 = soft(A^T y, lambda), so Delta_2 ~ 0 and both sides stop
+    after exactly 2 iterations; eps > 1 stops before the first iteration."""
+    N = 64
+    Q = rand_orthogonal(N, 9)
+    Y = sy.noise(70, N, 1.0, 9).astype(np.float32)
+    ctx = cs.cs_create(N, N, A=Q)
+    Xg, it, cv = gpu_run(cs.cs_recover_fista, ctx, Y, N, 0.3, 100, eps=1e-4)
+    Xo, ito = orc.fista(Q, Y, orc.lipschitz(Q), 0.3, 1e-4, 100)
+    assert np.all(ito == 2) and np.all(it == 2) and np.all(cv == 1)
+    assert rel_l2(Xg, soft_np(Y.astype(np.float64) @ Q, 0.3)) < 1e-5
+    Xg, it, cv = gpu_run(cs.cs_recover_fista, ctx, Y, N, 0.3, 100, eps=2.0)
+    assert np.all(Xg == 0) and np.all(it == 0)
+
+
+# --------------------------------------------------------------------------- ADMM
+@pytest.mark.parametrize("rho", [1.0, 1.8])
+def test_admm_small(cs, small, rho):
+    Xo, _ = orc.admm(small.A, small.Y, rho, 1e-3, 0.0, 500)
+    ctx = cs.cs_create(small.M, small.N, Phi=small.Phi, admm_rho=1.0)
+    Xg, it, cv = gpu_run(cs.cs_recover_admm, ctx, small.Y, small.N, rho, 1e-3, 500, eps=0.0)
+    assert rel_l2(Xg, Xo) <= REL_L2_FP32
+    assert np.all(it == 500)
+
+
+def test_admm_powerlaw(cs, plaw):
+    Xo, _ = orc.admm(plaw.A, plaw.Y, 1.0, 1e-3, 0.0, 300)
+    ctx = cs.cs_create(plaw.M, plaw.N, Phi=plaw.Phi, admm_rho=1.0)
+    Xg, _, _ = gpu_run(cs.cs_recover_admm, ctx, plaw.Y, plaw.N, 1.0, 1e-3, 300, eps=0.0)
+    assert rel_l2(Xg, Xo) <= REL_L2_FP32
+
+
+def test_admm_orthonormal_fixed_point(cs):
+    N = 64
+    Q = rand_orthogonal(N, 10)
+    Y = sy.noise(40, N, 1.0, 10).astype(np.float32)
+    ctx = cs.cs_create(N, N, A=Q)
+    Xg, _, _ = gpu_run(cs.cs_recover_admm, ctx, Y, N, 1.8, 0.3, 400, eps=0.0)
+    assert rel_l2(Xg, soft_np(Y.astype(np.float64) @ Q, 0.3)) < 1e-5
+
+
+# --------------------------------------------------------------------------- greedy
+def test_gomp_small(cs, small):
+    Xo, ito, mg = orc.gomp(small.A, small.Y, 8, 2)
+    ctx = cs.cs_create(small.M, small.N, Phi=small.Phi)
+    Xg, it, cv = gpu_run(cs.cs_recover_gomp, ctx, small.Y, small.N, 8, 2)
+    sep = support_check(Xg, Xo, mg, 8)
+    assert np.all(it[sep] == ito[sep])
+
+
+def test_gomp_powerlaw(cs, plaw):
+    Xo, ito, mg = orc.gomp(plaw.A, plaw.Y, 20, 4)
+    ctx = cs.cs_create(plaw.M, plaw.N, Phi=plaw.Phi)
+    Xg, it, cv = gpu_run(cs.cs_recover_gomp, ctx, plaw.Y, plaw.N, 20, 4)
+    sep = support_check(Xg, Xo, mg, 20)
+    assert np.all(it[sep] == ito[sep])
+
+
+def test_gomp_is_omp_exact(cs):
+    """gOMP with G = 1 on [I | H/8]: OMP recovers every 4-sparse x exactly."""
+    import scipy.linalg
+    M = 64
+    A = np.hstack([np.eye(M), scipy.linalg.hadamard(M) / 8.0])
+    Xt = sy.sparse_coeffs(100, 2 * M, 4, 11)
+    Y = (Xt @ A.T).astype(np.float32)
+    ctx = cs.cs_create(M, 2 * M, A=A)
+    Xg, _, _ = gpu_run(cs.cs_recover_gomp, ctx, Y, 2 * M, 4, 1)
+    assert np.all(support(Xg) == (Xt != 0))
+    assert rel_l2(Xg, Xt) < 1e-6
+
+
+@pytest.mark.parametrize("mu", [0.1, 1.0])
+def test_biht_small(cs, small, mu):
+    Xo, ito, mg = orc.biht(small.A, small.Y, 8, mu)
+    ctx = cs.cs_create(small.M, small.N, Phi=small.Phi)
+    Xg, it, cv = gpu_run(cs.cs_recover_biht, ctx, small.Y, small.N, 8, mu=mu)
+    sep = support_check(Xg, Xo, mg, 8)
+    assert np.all(it[sep] == ito[sep])
+
+
+def test_biht_powerlaw(cs, plaw):
+    Xo, ito, mg = orc.biht(plaw.A, plaw.Y, 20, 0.1)
+    ctx = cs.cs_create(plaw.M, plaw.N, Phi=plaw.Phi)
+    Xg, it, _ = gpu_run(cs.cs_recover_biht, ctx, plaw.Y, plaw.N, 20, mu=0.1)
+    sep = support_check(Xg, Xo, mg, 20)
+    assert np.all(it[sep] == ito[sep])
+
+
+def test_biht_worked_example(cs):
+    A = np.array([[1.0, 0.0, 1.0], [0.0, 1.0, 1.0]])
+    Y = np.array([[1.0, 3.0]], dtype=np.float32)
+    ctx = cs.cs_create(2, 3, A=A)
+    Xg, it, _ = gpu_run(cs.cs_recover_biht, ctx, Y, 3, 1, mu=2.0)
+    assert np.abs(Xg[0] - [0.0, 0.0, 3.0]).max() < 1e-6 and it[0] == 3
+
+
+def test_cosamp_small(cs, small):
+    Xo, ito, mg = orc.cosamp(small.A, small.Y, 8)
+    ctx = cs.cs_create(small.M, small.N, Phi=small.Phi)
+    Xg, it, cv = gpu_run(cs.cs_recover_cosamp, ctx, small.Y, small.N, 8)
+    sep = support_check(Xg, Xo, mg, 8)
+    assert np.all(it[sep] == ito[sep])
+
+
+def test_cosamp_powerlaw(cs):
+    # the 2 kappa = 40-atom cut of power-law spectra is often near-tied: take more pixels
+    plaw = Problem(80, 200, 32 * 40 + 5, "powerlaw", seed=2, noise_var=1e-3)
+    Xo, ito, mg = orc.cosamp(plaw.A, plaw.Y, 20)
+    ctx = cs.cs_create(plaw.M, plaw.N, Phi=plaw.Phi)
+    Xg, it, _ = gpu_run(cs.cs_recover_cosamp, ctx, plaw.Y, plaw.N, 20)
+    sep = support_check(Xg, Xo, mg, 20)
+    assert np.all(it[sep] == ito[sep])
+
+
+def test_min_norm_support(cs):
+    """CoSaMP with 3 kappa > M: supports larger than M take the minimum-norm solution."""
+    pr = Problem(24, 60, 70, "sparse", seed=12, S=10)
+    Xo, ito, mg = orc.cosamp(pr.A, pr.Y, 10, max_iters=5)
+    ctx = cs.cs_create(pr.M, pr.N, Phi=pr.Phi)
+    Xg, it, _ = gpu_run(cs.cs_recover_cosamp, ctx, pr.Y, pr.N, 10, max_iters=5)
+    sep = mg > MARGIN_FP32
+    same = np.all(support(Xg[sep]) == support(Xo[sep]), axis=1)
+    assert same.mean() > 0.9
+    assert rel_l2(Xg[sep][same], Xo[sep][same]) < 1e-4
+
+
+def test_kappa_per_pixel(cs):
+    """Per-pixel sparsity with G = max(1, floor(kappa/5)) (the paper's G rule)."""
+    pr = Problem(48, 120, 200, "sparse", seed=13, S=6, amplitude="separated")
+    kp = sy.kappa_per_pixel(pr.P, 4, 12, 13)
+    ctx = cs.cs_create(pr.M, pr.N, Phi=pr.Phi)
+    Xg, it, _ = gpu_run(cs.cs_recover_gomp, ctx, pr.Y, pr.N, 12, 0, kappa_pp=kp)
+    Xo = np.zeros_like(pr.Xt)
+    mg = np.zeros(pr.P)
+    for k in np.unique(kp):
+        sel = kp == k
+        Xo[sel], _, mg[sel] = orc.gomp(pr.A, pr.Y[sel], int(k), max(1, int(k) // 5))
+    support_check(Xg, Xo, mg, 12)
+
+
+# --------------------------------------------------------------------------- edges
+def test_edge_cases(cs, small):
+    torch = pytest.importorskip("torch")
+    ctx = cs.cs_create(small.M, small.N, Phi=small.Phi)
+    Y = small.Y[:40].copy()
+    Y[3] = 0.0  # y = 0 -> x = 0 for every method
+    for call, args in [(cs.cs_recover_fista, (1e-3, 50)), (cs.cs_recover_admm, (1.0, 1e-3, 50)),
+                       (cs.cs_recover_gomp, (8, 2)), (cs.cs_recover_biht, (8,)),
+                       (cs.cs_recover_cosamp, (8,))]:
+        Xg, it, _ = gpu_run(call, ctx, Y, small.N, *args)
+        assert np.all(Xg[3] == 0), call.__name__
+        assert np.all(np.isfinite(Xg))
+    Xg, it, _ = gpu_run(cs.cs_recover_gomp, ctx, Y, small.N, 0, 2)  # kappa = 0
+    assert np.all(Xg == 0) and np.all(it == 0)
+    # P = 0 is a no-op
+    e = torch.zeros((0, small.M), device="cuda")
+    cs.cs_recover_fista(ctx, e, torch.zeros((0, small.N), device="cuda"), 1e-3, 10)
+    cs.cs_sync(ctx)
+    # a single pixel
+    Xg, _, _ = gpu_run(cs.cs_recover_gomp, ctx, small.Y[:1], small.N, 8, 2)
+    Xo, _, _ = orc.gomp(small.A, small.Y[:1], 8, 2)
+    assert rel_l2(Xg, Xo) < 1e-5
+
+
+def test_nonfinite_input_is_reported(cs, small):
+    torch = pytest.importorskip("torch")
+    ctx = cs.cs_create(small.M, small.N, Phi=small.Phi)
+    Y = small.Y[:8].copy()
+    Y[2, 5] = np.nan
+    X = torch.zeros((8, small.N), device="cuda")
+    cs.cs_recover_gomp(ctx, torch.from_numpy(Y).cuda(), X, 8, 2)
+    with pytest.raises(cs.CsError) as e:
+        cs.cs_sync(ctx)
+    assert e.value.status == cs.CS_ERR_NONFINITE
+    cs.cs_sync(ctx)  # the status word was cleared
+
+
+def test_host_pointer_path_matches_device(cs, small):
+    ctx = cs.cs_create(small.M, small.N, Phi=small.Phi)
+    Xh = np.zeros((small.P, small.N), dtype=np.float32)
+    cs.cs_recover_fista(ctx, small.Y, Xh, 1e-3, 100, opts=cs.make_opts(eps=0.0))
+    Xd, _, _ = gpu_run(cs.cs_recover_fista, ctx, small.Y, small.N, 1e-3, 100, eps=0.0)
+    assert np.array_equal(Xh, Xd)
+    Xh = np.zeros((small.P, small.N), dtype=np.float32)
+    cs.cs_recover_gomp(ctx, small.Y, Xh, 8, 2)
+    Xd, _, _ = gpu_run(cs.cs_recover_gomp, ctx, small.Y, small.N, 8, 2)
+    assert np.array_equal(Xh, Xd)
+
+
+def test_argument_errors(cs, small):
+    torch = pytest.importorskip("torch")
+    ctx = cs.cs_create(small.M, small.N, Phi=small.Phi)
+    Y = torch.zeros((4, small.M), device="cuda")
+    X = torch.zeros((4, small.N), device="cuda")
+    bad = [lambda: cs.cs_recover_fista(ctx, Y, X, -1.0, 10),
+           lambda: cs.cs_recover_fista(ctx, Y, X, 0.1, -1),
+           lambda: cs.cs_recover_admm(ctx, Y, X, 0.0, 0.1, 10),
+           lambda: cs.cs_recover_gomp(ctx, Y, X, small.N + 1, 2),
+           lambda: cs.cs_recover_gomp(ctx, Y, X, 8, 0),
+           lambda: cs.cs_recover_cosamp(ctx, Y, X, small.N // 2 + 1),
+           lambda: cs.cs_recover_fista(ctx, Y, X.cpu().numpy(), 0.1, 10),
+           lambda: cs.cs_recover_fista(ctx, Y, X, 0.1, 10, opts=cs.make_opts(eps=-1.0))]
+    for f in bad:
+        with pytest.raises(cs.CsError) as e:
+            f()
+        assert e.value.status == cs.CS_ERR_ARG
