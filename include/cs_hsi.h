@@ -136,6 +136,25 @@ cs_status cs_recover_biht(cs_ctx *ctx, const float *Y, float *X, int64_t P, int 
 cs_status cs_recover_cosamp(cs_ctx *ctx, const float *Y, float *X, int64_t P, int kappa,
                             const cs_opts *opts);
 
+/* gOMP exactly as cs_recover_gomp, for callers that cannot allocate device memory when
+ * they recover a cube -- for example code whose device memory is all handed to its own
+ * pool, or that cannot afford the device-wide synchronisation of cudaMalloc/cudaFree.
+ * It needs no context and allocates nothing: the caller passes the FP64 dictionary
+ * A_dev (M x N, row-major, e.g. from cs_get_dictionary) and the cube Y, X, all in
+ * device memory it owns (host memory is rejected: staging it would allocate).  The
+ * FP32/transposed copies of A, the FP64 Gram matrix and the kernel's work counter live
+ * in one static device array of 1 MiB that every GPU loading the library holds until
+ * exit; M x N shapes needing more (16 M N + 8 N^2 bytes plus alignment, e.g. M = 128
+ * with N = 256) return CS_ERR_SHAPE.  The first call on a device looks up that array's
+ * address; make it before any stream capture.  Every call re-derives the scratch
+ * contents and resets the counter, and all calls share the one array: calls that
+ * overlap on the GPU race and must be ordered by the caller.  Asynchronous on `stream`;
+ * device-side conditions are reported only through opts->converged_out (2 = LS failure).
+ * The paper has no counterpart of this entry point. */
+cs_status cs_recover_gomp_noalloc(const double *A_dev, int M, int N, const float *Y, float *X,
+                                  int64_t P, int kappa, int G, const cs_opts *opts,
+                                  void *stream);
+
 /* Waits for the context's stream and returns (and clears) the latched device status. */
 cs_status cs_sync(cs_ctx *ctx);
 

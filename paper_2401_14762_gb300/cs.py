@@ -21,7 +21,8 @@ CS_FP32, CS_BF16, CS_FP8_E4M3 = 0, 1, 2
 
 EXPORTED = ["cs_opts_default", "cs_create", "cs_destroy", "cs_get_lipschitz", "cs_get_dictionary",
             "cs_measure", "cs_recover_fista", "cs_recover_admm", "cs_recover_gomp",
-            "cs_recover_biht", "cs_recover_cosamp", "cs_sync", "cs_last_error"]
+            "cs_recover_biht", "cs_recover_cosamp", "cs_recover_gomp_noalloc", "cs_sync",
+            "cs_last_error"]
 
 
 class CsError(RuntimeError):
@@ -63,6 +64,7 @@ def load_library(path: str = LIB_PATH):
     lib.cs_recover_gomp.argtypes = [vp, vp, vp, i64, i32, i32, op]
     lib.cs_recover_biht.argtypes = [vp, vp, vp, i64, i32, op]
     lib.cs_recover_cosamp.argtypes = [vp, vp, vp, i64, i32, op]
+    lib.cs_recover_gomp_noalloc.argtypes = [vp, i32, i32, vp, vp, i64, i32, i32, op, vp]
     lib.cs_sync.argtypes = [vp]
     lib.cs_last_error.argtypes = []
     lib.cs_last_error.restype = ctypes.c_char_p
@@ -235,6 +237,18 @@ def cs_recover_cosamp(ctx: Context, Y, X, kappa, opts: cs_opts | None = None, P=
     _check(load_library().cs_recover_cosamp(ctx.handle, _ptr(Y, np.float32), _ptr(X, np.float32),
                                             int(P), int(kappa),
                                             ctypes.byref(opts) if opts else None))
+    return X
+
+
+def cs_recover_gomp_noalloc(A_dev, M, N, Y, X, kappa, G, opts: cs_opts | None = None, P=None,
+                            stream=None):
+    """gOMP without a context or any device allocation (for callers that cannot allocate);
+    A_dev, Y and X are device arrays the caller owns."""
+    P = _rows(Y) if P is None else P
+    _check(load_library().cs_recover_gomp_noalloc(
+        _ptr(A_dev, np.float64), int(M), int(N), _ptr(Y, np.float32), _ptr(X, np.float32),
+        int(P), int(kappa), int(G), ctypes.byref(opts) if opts else None,
+        stream if stream is not None else _default_stream()))
     return X
 
 

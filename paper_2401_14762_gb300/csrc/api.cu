@@ -330,6 +330,57 @@ cs_status cs_recover_cosamp(cs_ctx* ctx, const float* Y, float* X, int64_t P, in
   return greedy(ctx, cs::kCosamp, Y, X, P, kappa, 0, opts);
 }
 
+cs_status cs_recover_gomp_noalloc(const double* A_dev, int M, int N, const float* Y, float* X,
+                                  int64_t P, int kappa, int G, const cs_opts* opts,
+                                  void* stream) {
+  cs::set_error("");
+  cs_opts o;
+  cs_opts_default(&o);
+  if (opts) o = *opts;
+  if (M < 1 || N < 1 || M > N || M > cs::kMaxM || N > cs::kMaxN) {
+    cs::set_error("need 1 <= M <= N, M <= 128, N <= 256");
+    return CS_ERR_SHAPE;
+  }
+  size_t need = cs::noalloc_scratch_bytes(M, N), have = cs::noalloc_scratch_capacity();
+  if (need > have) {
+    cs::set_error("this M x N dictionary needs " + std::to_string(need) +
+                  " bytes of static scratch; cs_recover_gomp_noalloc holds " +
+                  std::to_string(have) + " (use cs_recover_gomp)");
+    return CS_ERR_SHAPE;
+  }
+  if (P < 0) return arg_error("P < 0");
+  if (P > ((int64_t)1 << 31) - 1) {
+    cs::set_error("P must be below 2^31");
+    return CS_ERR_SHAPE;
+  }
+  if (!A_dev || (P > 0 && (!Y || !X))) return arg_error("A, Y or X is NULL");
+  if (!cs::is_device_ptr(A_dev) || (P > 0 && (!cs::is_device_ptr(Y) || !cs::is_device_ptr(X))))
+    return arg_error("cs_recover_gomp_noalloc takes device memory only (staging host memory "
+                     "would allocate)");
+  if (!(o.eps >= 0.0) || !std::isfinite(o.eps)) return arg_error("eps must be >= 0");
+  if (o.max_iters < 0) return arg_error("max_iters < 0");
+  if ((o.iters_out && !cs::is_device_ptr(o.iters_out)) ||
+      (o.converged_out && !cs::is_device_ptr(o.converged_out)) ||
+      (o.kappa_per_pixel && !cs::is_device_ptr(o.kappa_per_pixel)))
+    return arg_error("per-pixel option arrays must be device memory");
+  if (kappa < 0 || kappa > N) return arg_error("kappa out of range");
+  if (G < 0 || G > N || (G == 0 && !o.kappa_per_pixel))
+    return arg_error("G must be in 1..N (0 only with kappa_per_pixel)");
+  int dev = 0, major = 0, minor = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
+  if (e != cudaSuccess || major != 10 || minor != 3) {
+    cs::set_error("needs a CUDA device of compute capability 10.3 (GB300)");
+    return CS_ERR_NO_DEVICE;
+  }
+  cs::GreedyArgs a{Y, X, P, kappa, G, o.mu, o.eps, o.max_iters, o.kappa_per_pixel, kappa,
+                   o.iters_out, o.converged_out, o.prec};
+  e = cs::launch_gomp_noalloc(A_dev, M, N, a, static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "cs_recover_gomp_noalloc");
+  return CS_OK;
+}
+
 cs_status cs_sync(cs_ctx* ctx) {
   if (cs_status s = cs::check_ctx(ctx)) return s;
   cs::Ctx& c = ctx->c;

@@ -96,6 +96,12 @@ struct GreedyArgs {
 };
 cudaError_t launch_greedy(const Ctx& c, GreedyAlgo algo, const GreedyArgs& a);
 
+// ---- allocation-free gOMP (scratch in a static device array) ----
+size_t noalloc_scratch_bytes(int M, int N);
+size_t noalloc_scratch_capacity();
+cudaError_t launch_gomp_noalloc(const double* A64, int M, int N, const GreedyArgs& a,
+                                cudaStream_t stream);
+
 // ---- warp helpers ----
 __device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll

@@ -21,6 +21,8 @@
 // stopping rule.  All per-pixel state sits in the warp's slice of shared memory.
 #include <cuda_runtime.h>
 
+#include <mutex>
+
 #include "cs_internal.cuh"
 
 namespace cs {
@@ -620,6 +622,166 @@ cudaError_t launch_greedy(const Ctx& c, GreedyAlgo algo, const GreedyArgs& a) {
   if (algo == kGomp) return launch(k_greedy<kGomp>);
   if (algo == kBiht) return launch(k_greedy<kBiht>);
   return launch(k_greedy<kCosamp>);
+}
+
+}  // namespace cs
+
+// ---------------------------------------------------------------------------------
+// Allocation-free gOMP (cs_recover_gomp_noalloc).
+//
+// Some callers cannot call cudaMalloc when they recover a cube: code that runs with
+// all device memory already handed to its own pool, or in a phase where the
+// device-wide synchronisation of cudaMalloc/cudaFree is not acceptable.  They pass
+// the FP64 dictionary, the measurements and the output (their own device memory);
+// everything else the gOMP kernel reads -- the FP32 and transposed copies of A, the
+// FP64 Gram matrix A^T A, the work counter and a status word -- lives in the
+// file-scope array below, which every GPU that loads this library holds until exit.
+// Each call re-derives that data, so all calls share one scratch: calls that overlap
+// on the GPU (different streams, different host threads) race and must be ordered by
+// the caller.
+// ---------------------------------------------------------------------------------
+constexpr size_t kNoAllocScratchBytes = (size_t)1 << 20;  // 1 MiB
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+namespace cs {
+namespace {
+
+struct NoAllocLayout {
+  size_t counter, status, A32, At32, At64, G64, total;
+  NoAllocLayout(int M, int N) {
+    size_t o = 0;
+    auto take = [&](size_t bytes) {
+      size_t at = o;
+      o += (bytes + 255) / 256 * 256;
+      return at;
+    };
+    counter = take(8);
+    status = counter + 8;
+    A32 = take(sizeof(float) * (size_t)M * N);
+    At32 = take(sizeof(float) * (size_t)M * N);
+    At64 = take(sizeof(double) * (size_t)M * N);
+    G64 = take(sizeof(double) * (size_t)N * N);
+    total = o;
+  }
+};
+
+// FP32 copy of A, its transposes in FP32 and FP64 (same values as the context setup).
+__global__ void k_noalloc_casts(int M, int N, const double* A, float* A32, float* At32,
+                                double* At64) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= M * N) return;
+  int m = i / N, n = i % N;
+  double a = A[i];
+  A32[i] = (float)a;
+  At64[n * M + m] = a;
+  At32[n * M + m] = (float)a;
+}
+
+// G[r][c] = sum_k A[k][r] A[k][c], summed in the same order as the context setup.
+__global__ void k_noalloc_gram(int M, int N, const double* A, double* G) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N * N) return;
+  int r = i / N, col = i % N;
+  double s = 0.0;
+  for (int k = 0; k < M; ++k) s += A[r + k * N] * A[k * N + col];
+  G[i] = s;
+}
+
+// Device address of g_noalloc_scratch on the current device, looked up once per device.
+constexpr int kMaxDevices = 64;
+struct ScratchAddr {
+  std::once_flag once;
+  unsigned char* ptr = nullptr;
+  cudaError_t err = cudaSuccess;
+};
+ScratchAddr g_scratch_addr[kMaxDevices];
+
+}  // namespace
+
+size_t noalloc_scratch_bytes(int M, int N) { return NoAllocLayout(M, N).total; }
+size_t noalloc_scratch_capacity() { return kNoAllocScratchBytes; }
+
+cudaError_t launch_gomp_noalloc(const double* A64, int M, int N, const GreedyArgs& a,
+                                cudaStream_t stream) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  ScratchAddr& sa = g_scratch_addr[dev];
+  std::call_once(sa.once, [&] {
+    void* p = nullptr;
+    sa.err = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    sa.ptr = static_cast<unsigned char*>(p);
+  });
+  if (sa.err != cudaSuccess) return sa.err;
+  NoAllocLayout lay(M, N);
+  if (lay.total > kNoAllocScratchBytes) return cudaErrorInvalidValue;
+  unsigned char* s = sa.ptr;
+  float* A32 = reinterpret_cast<float*>(s + lay.A32);
+  float* At32 = reinterpret_cast<float*>(s + lay.At32);
+  double* At64 = reinterpret_cast<double*>(s + lay.At64);
+  double* G64 = reinterpret_cast<double*>(s + lay.G64);
+  // the counter and the status word must start at zero on every call
+  e = cudaMemsetAsync(s + lay.counter, 0, 16, stream);
+  if (e != cudaSuccess) return e;
+  if (a.P == 0) return cudaSuccess;
+  k_noalloc_casts<<<(M * N + 255) / 256, 256, 0, stream>>>(M, N, A64, A32, At32, At64);
+  k_noalloc_gram<<<(N * N + 255) / 256, 256, 0, stream>>>(M, N, A64, G64);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+
+  int num_sms = 0;
+  e = cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  GrParams p{};
+  p.M = M;
+  p.N = N;
+  p.algo = kGomp;
+  p.A32 = A32;
+  p.At32 = At32;
+  p.At64 = At64;
+  p.G64 = G64;
+  p.Y = a.Y;
+  p.X = a.X;
+  p.P = a.P;
+  p.kappa = a.kappa;
+  p.G = a.G;
+  p.kappa_pp = a.kappa_pp;
+  p.mu = (float)a.mu;
+  p.eps2 = a.eps * a.eps;
+  p.start_done = a.eps > 1.0;
+  p.max_iters = a.max_iters;
+  p.iters_out = a.iters_out;
+  p.conv_out = a.conv_out;
+  p.status = reinterpret_cast<int*>(s + lay.status);
+  p.counter = reinterpret_cast<unsigned long long*>(s + lay.counter);
+  const int K = a.kappa_max;
+  int gmax = a.G > 0 ? a.G : (K / 5 > 1 ? K / 5 : 1);
+  int iters = a.max_iters < K ? a.max_iters : K;
+  long long cm = (long long)gmax * (iters > 0 ? iters : 1);
+  int cmax = (int)(cm < M ? cm : M);
+  if (a.G == 0) cmax = M;
+  if (cmax < 1) cmax = 1;
+  p.cmax = cmax;
+  p.dmax = cmax < M ? cmax : M;
+  p.kmax = K > 0 ? K : 1;
+  Layout wl(M, N, p.cmax, p.dmax, p.kmax);
+  p.warp_bytes = wl.total;
+  int warps = (220 * 1024) / wl.total;
+  if (warps > 8) warps = 8;
+  if (warps < 1) return cudaErrorInvalidConfiguration;
+  size_t smem = (size_t)warps * wl.total;
+  auto kern = k_greedy<kGomp>;
+  e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, warps * 32, smem);
+  if (per_sm < 1) per_sm = 1;
+  long long grid = (long long)num_sms * per_sm;
+  long long need = (a.P + warps - 1) / warps;
+  if (grid > need) grid = need;
+  kern<<<(unsigned)grid, warps * 32, smem, stream>>>(p);
+  return cudaGetLastError();
 }
 
 }  // namespace cs
