@@ -50,6 +50,7 @@ void free_ctx(Ctx& c) {
   cudaFree(c.stage_in);
   cudaFree(c.stage_out);
   cudaFree(c.stage_aux);
+  cudaFree(c.fb64);
 }
 
 // Is ptr device-accessible memory (cudaMalloc / managed)?  Host memory, pinned or not,

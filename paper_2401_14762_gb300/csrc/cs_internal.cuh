@@ -44,6 +44,8 @@ struct Ctx {
   size_t scratch_elems = 0;
   int* status = nullptr;      // device status word
   int* counter = nullptr;     // work counter of the persistent greedy kernel
+  double* fb64 = nullptr;     // per-warp FP64 fallback slots of the greedy kernel
+  size_t fb64_elems = 0;
   float* stage_in = nullptr;  // staging for host-pointer calls
   float* stage_out = nullptr;
   float* stage_aux = nullptr;
@@ -94,7 +96,7 @@ struct GreedyArgs {
   uint8_t* conv_out;
   cs_precision prec;
 };
-cudaError_t launch_greedy(const Ctx& c, GreedyAlgo algo, const GreedyArgs& a);
+cudaError_t launch_greedy(Ctx& c, GreedyAlgo algo, const GreedyArgs& a);
 
 // ---- allocation-free gOMP (scratch in a static device array) ----
 size_t noalloc_scratch_bytes(int M, int N);

@@ -51,13 +51,19 @@ struct GrParams {
   uint8_t* conv_out;
   int* status;
   unsigned long long* counter;
+  double* fb64;      // per-warp global FP64 fallback slots (nullptr: FP64 factors in smem)
+  int fb_slot;       // doubles per slot
 };
 
-// Byte offsets of one warp's shared-memory slice.
+// Byte offsets of one warp's shared-memory slice.  With fp64_smem the factor regions are
+// sized for FP64 (the fallback factorisation then runs in place); otherwise they hold
+// the FP32 factors only and the fallback uses the warp's global slot.
 struct Layout {
-  int y, r, xd, b, bflag, inc, c, q, sel, tmp16, xq, L, invd, v, s, wv, Lq, invq, vq, sq,
+  int y, rf, r, xd, b, bflag, inc, c, q, sel, tmp16, xq, L, invd, v, s, wv, Lq, invq, vq, sq,
       svals, total;
-  __host__ __device__ Layout(int M, int N, int cmax, int dmax, int kmax) {
+  __host__ __device__ Layout(int M, int N, int cmax, int dmax, int kmax, bool fp64_smem,
+                             bool need_q) {
+    const int fw = fp64_smem ? 8 : 4;
     int o = 0;
     auto take = [&](int bytes, int align) {
       o = (o + align - 1) / align * align;
@@ -67,18 +73,20 @@ struct Layout {
     };
     b = take(8 * N, 8);
     xq = take(8 * kmax, 8);
-    L = take(8 * (dmax * (dmax + 1) / 2), 8);
+    L = take(fw * (dmax * (dmax + 1) / 2), 8);
     invd = take(8 * dmax, 8);
     v = take(8 * dmax, 8);
     s = take(8 * cmax, 8);
-    wv = take(8 * N, 8);
-    Lq = take(8 * (kmax * (kmax + 1) / 2), 8);
-    invq = take(8 * kmax, 8);
-    vq = take(8 * kmax, 8);
-    sq = take(8 * kmax, 8);
+    wv = take(8 * dmax, 8);
+    const int kq = need_q ? kmax : 0;
+    Lq = take(fw * (kq * (kq + 1) / 2), 8);
+    invq = take(8 * kq, 8);
+    vq = take(8 * kq, 8);
+    sq = take(8 * kq, 8);
     svals = take(8 * cmax, 8);
     r = take(8 * M, 8);
     y = take(4 * M, 4);
+    rf = take(4 * M, 4);
     xd = take(4 * N, 4);
     c = take(2 * cmax, 2);
     q = take(2 * kmax, 2);
@@ -97,10 +105,11 @@ __device__ __forceinline__ int lidx(int t, int i, int cap) { return i * cap - i 
 struct Warp {
   const GrParams& p;
   int lane;
-  float *y, *xd;
+  float *y, *rf, *xd;
   double *r, *b, *xq, *L, *invd, *v, *s, *wv, *Lq, *invq, *vq, *sq, *svals;
   uint8_t *bflag, *inc;
   int16_t *c, *q, *sel, *tmp16;
+  double* fb;  // this warp's global FP64 fallback slot, or nullptr
 };
 
 // (A^T y)_j in FP64, computed once per pixel and atom.
@@ -177,6 +186,282 @@ __device__ void back_solve(Warp& w, const double* L, const double* invd, const d
   }
 }
 
+// ---------------------------------------------------------------------------------
+// Mixed-precision support least squares: FP32 Cholesky of G_c, FP32 triangular solves
+// on vectors held in registers (lane l owns entries l, l+32, ...), and FP64 iterative
+// refinement s <- s + G_c^{-1}(b - G_c s) whose residual uses the FP64 Gram matrix.
+// FP64 work per solve is one or two n^2 residuals instead of an n^3/3 factorisation,
+// which matters on GB300, whose FP64 rate is 1/64 of its FP32 rate.
+// ---------------------------------------------------------------------------------
+template <int VR, typename T>
+__device__ __forceinline__ T rpick(const T (&v)[VR], int slot) {
+  T r = v[0];
+#pragma unroll
+  for (int k = 1; k < VR; ++k)
+    if (slot == k) r = v[k];
+  return r;
+}
+
+__device__ __forceinline__ float warp_max(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// (A^T y)_j in FP64 for every atom of atoms[0..n) into out[0..n); lanes take atoms, so
+// no reductions are needed; values are cached per pixel.
+__device__ void fill_rhs(Warp& w, const int16_t* atoms, int n, double* out) {
+  const int M = w.p.M;
+  for (int t = w.lane; t < n; t += 32) {
+    int a = atoms[t];
+    double v;
+    if (w.bflag[a]) {
+      v = w.b[a];
+    } else {
+      const double* col = w.p.At64 + (size_t)a * M;
+      v = 0.0;
+      for (int m = 0; m < M; ++m) v += col[m] * (double)w.y[m];
+      w.b[a] = v;
+      w.bflag[a] = 1;
+    }
+    out[t] = v;
+  }
+  __syncwarp();
+}
+
+// Gathers G_c (FP32) into the packed column-major lower triangle L and factors it in
+// place, right-looking.  Lane l owns rows l, l+32, ...; at step j the column values
+// L(k, j) reach every lane by shuffle, so the trailing update L(i, k) -= L(i, j) L(k, j)
+// runs in lock step over k with conflict-free shared-memory traffic.  Returns false when
+// a pivot drops below 1e-4 of its original diagonal (FP32 would lose the factor).
+template <int VR>
+__device__ bool chol32(Warp& w, float* L, float* invd, int cap, int n, const int16_t* atoms) {
+  const int lane = w.lane, N = w.p.N;
+  const double* G = w.p.G64;
+  for (int k = 0; k < n; ++k) {
+    const double* grow = G + (size_t)atoms[k] * N;
+    const int ck = lidx(0, k, cap);
+    for (int i = k + lane; i < n; i += 32) {
+      float g = (float)grow[atoms[i]];
+      L[ck + i] = g;
+      if (i == k) invd[k] = g;  // original diagonal, for the pivot test
+    }
+  }
+  __syncwarp();
+  for (int j = 0; j < n; ++j) {
+    const int cj = lidx(0, j, cap);
+    float d = L[cj + j];
+    if (!(d > 1e-4f * invd[j])) return false;  // warp-uniform
+    float dj = sqrtf(d), inv = 1.f / dj;
+    float lij[VR];
+#pragma unroll
+    for (int r = 0; r < VR; ++r) {
+      int i = lane + 32 * r;
+      lij[r] = 0.f;
+      if (i > j && i < n) {
+        lij[r] = L[cj + i] * inv;
+        L[cj + i] = lij[r];
+      }
+    }
+    if (lane == 0) {
+      L[cj + j] = dj;
+      invd[j] = inv;
+    }
+    int ck = lidx(0, j + 1, cap);
+#pragma unroll 4
+    for (int k = j + 1; k < n; ++k) {
+      float lkj = __shfl_sync(0xffffffffu, rpick<VR>(lij, k >> 5), k & 31);
+#pragma unroll
+      for (int r = 0; r < VR; ++r) {
+        int i = lane + 32 * r;
+        if (32 * r + 31 >= k && i >= k && i < n) L[ck + i] = fmaf(-lij[r], lkj, L[ck + i]);
+      }
+      ck += cap - k - 1;
+    }
+    __syncwarp();
+  }
+  return true;
+}
+
+// v := L^{-1} v and v := L^{-T} v on register-distributed vectors.
+template <int VR>
+__device__ void fwd32(const float* L, const float* invd, int cap, int n, float (&v)[VR], int lane) {
+  for (int i = 0; i < n; ++i) {
+    float vi = __shfl_sync(0xffffffffu, rpick<VR>(v, i >> 5), i & 31) * invd[i];
+    const float* col = L + lidx(0, i, cap);
+#pragma unroll
+    for (int k = 0; k < VR; ++k) {
+      int t = lane + 32 * k;
+      if (t == i) v[k] = vi;
+      else if (t > i && t < n) v[k] = fmaf(-col[t], vi, v[k]);
+    }
+  }
+}
+template <int VR>
+__device__ void bwd32(const float* L, const float* invd, int cap, int n, float (&v)[VR], int lane) {
+  for (int i = n - 1; i >= 0; --i) {
+    float si = __shfl_sync(0xffffffffu, rpick<VR>(v, i >> 5), i & 31) * invd[i];
+#pragma unroll
+    for (int k = 0; k < VR; ++k) {
+      int t = lane + 32 * k;
+      if (t == i) v[k] = si;
+      else if (t < i) v[k] = fmaf(-L[lidx(i, t, cap)], si, v[k]);
+    }
+  }
+}
+
+// Iterative refinement on the FP32 factor: returns true once a correction falls below
+// 1e-9 of the solution (the solution then carries FP64-level accuracy), false if the
+// corrections stop contracting (the system is too ill-conditioned for an FP32 factor).
+template <int VR>
+__device__ bool refine32(Warp& w, const float* L, const float* invd, int cap, int n,
+                         const int16_t* atoms, const double* b, double* s) {
+  const int lane = w.lane, N = w.p.N;
+  const double* G = w.p.G64;
+  double sr[VR], rr[VR];
+#pragma unroll
+  for (int k = 0; k < VR; ++k) {
+    int t = lane + 32 * k;
+    sr[k] = 0.0;
+    rr[k] = t < n ? b[t] : 0.0;
+  }
+  float prev = 3.0e38f;
+  for (int step = 0; step < 5; ++step) {
+    float f[VR];
+#pragma unroll
+    for (int k = 0; k < VR; ++k) f[k] = (float)rr[k];
+    fwd32<VR>(L, invd, cap, n, f, lane);
+    bwd32<VR>(L, invd, cap, n, f, lane);
+    float dm = 0.f;
+    double sm = 0.0;
+#pragma unroll
+    for (int k = 0; k < VR; ++k) {
+      int t = lane + 32 * k;
+      if (t < n) {
+        sr[k] += (double)f[k];
+        dm = fmaxf(dm, fabsf(f[k]));
+        sm = fmax(sm, fabs(sr[k]));
+        s[t] = sr[k];
+      }
+    }
+    dm = warp_max(dm);
+    sm = warp_max(sm);
+    __syncwarp();
+    if ((double)dm <= 1e-9 * sm) return true;
+    if (step > 0 && dm > 0.5f * prev) return false;
+    prev = dm;
+    // r = b - G_c s in FP64
+#pragma unroll
+    for (int k = 0; k < VR; ++k) {
+      int t = lane + 32 * k;
+      if (t < n) {
+        const double* grow = G + (size_t)atoms[t] * N;
+        double a0 = b[t], a1 = 0.0, a2 = 0.0, a3 = 0.0;
+        int j = 0;
+        for (; j + 3 < n; j += 4) {
+          a0 -= grow[atoms[j]] * s[j];
+          a1 -= grow[atoms[j + 1]] * s[j + 1];
+          a2 -= grow[atoms[j + 2]] * s[j + 2];
+          a3 -= grow[atoms[j + 3]] * s[j + 3];
+        }
+        for (; j < n; ++j) a0 -= grow[atoms[j]] * s[j];
+        rr[k] = (a0 + a1) + (a2 + a3);
+      }
+    }
+  }
+  return false;
+}
+
+// Least squares on atoms[0..n) (n <= M): mixed precision first, FP64 factorisation if
+// the FP32 factor fails.  b goes to vbuf; Lbuf/invdbuf hold FP32 or FP64 factors.
+template <int VR>
+__device__ bool ls_solve(Warp& w, const int16_t* atoms, int n, double* Lbuf, double* invdbuf,
+                         double* vbuf, double* s, int cap);
+
+// The k largest |val| over atoms lane + 32 kk < nvalid, ties to the lower atom: a bitwise
+// search for the k-th largest magnitude (IEEE bits of |v| order like the values), then a
+// ballot compaction of everything above it plus the lowest-indexed ties.  32 warp steps
+// whatever k is; output in ascending atom order.
+__device__ void topk_select_atoms(Warp& w, const float (&val)[kNK], int nvalid, int k,
+                                  int16_t* out) {
+  const int lane = w.lane;
+  unsigned key[kNK];
+  bool ok[kNK];
+#pragma unroll
+  for (int kk = 0; kk < kNK; ++kk) {
+    ok[kk] = lane + 32 * kk < nvalid;
+    key[kk] = __float_as_uint(fabsf(val[kk]));
+  }
+  unsigned T = 0;
+  for (int b = 31; b >= 0; --b) {
+    unsigned cand = T | (1u << b), cnt = 0;
+#pragma unroll
+    for (int kk = 0; kk < kNK; ++kk) cnt += (ok[kk] && key[kk] >= cand) ? 1u : 0u;
+    if (__reduce_add_sync(0xffffffffu, cnt) >= (unsigned)k) T = cand;
+  }
+  unsigned gt = 0;
+#pragma unroll
+  for (int kk = 0; kk < kNK; ++kk) gt += (ok[kk] && key[kk] > T) ? 1u : 0u;
+  const int need = k - (int)__reduce_add_sync(0xffffffffu, gt);
+  const unsigned below = (1u << lane) - 1u;
+  int pos = 0, eq_before = 0;
+#pragma unroll
+  for (int kk = 0; kk < kNK; ++kk) {
+    bool isgt = ok[kk] && key[kk] > T, iseq = ok[kk] && key[kk] == T;
+    unsigned eqm = __ballot_sync(0xffffffffu, iseq);
+    bool take = isgt || (iseq && eq_before + __popc(eqm & below) < need);
+    unsigned tm = __ballot_sync(0xffffffffu, take);
+    if (take) out[pos + __popc(tm & below)] = (int16_t)(lane + 32 * kk);
+    pos += __popc(tm);
+    eq_before += __popc(eqm);
+  }
+  __syncwarp();
+}
+
+// The k largest |vals[p]| over positions p < cnt (FP64, ties to the lower position),
+// by the same bitwise search on the 64-bit patterns.  Output in ascending position order.
+__device__ void topk_select_positions(Warp& w, const double* vals, int cnt, int k, int16_t* out) {
+  const int lane = w.lane;
+  unsigned long long key[kNK];
+  bool ok[kNK];
+#pragma unroll
+  for (int kk = 0; kk < kNK; ++kk) {
+    int p = lane + 32 * kk;
+    ok[kk] = p < cnt;
+    key[kk] = ok[kk] ? (unsigned long long)__double_as_longlong(fabs(vals[p])) : 0ull;
+  }
+  unsigned long long T = 0;
+  for (int b = 63; b >= 0; --b) {
+    unsigned long long cand = T | (1ull << b);
+    unsigned c = 0;
+#pragma unroll
+    for (int kk = 0; kk < kNK; ++kk) c += (ok[kk] && key[kk] >= cand) ? 1u : 0u;
+    if (__reduce_add_sync(0xffffffffu, c) >= (unsigned)k) T = cand;
+  }
+  unsigned gt = 0;
+#pragma unroll
+  for (int kk = 0; kk < kNK; ++kk) gt += (ok[kk] && key[kk] > T) ? 1u : 0u;
+  const int need = k - (int)__reduce_add_sync(0xffffffffu, gt);
+  const unsigned below = (1u << lane) - 1u;
+  int pos = 0, eq_before = 0;
+#pragma unroll
+  for (int kk = 0; kk < kNK; ++kk) {
+    bool isgt = ok[kk] && key[kk] > T, iseq = ok[kk] && key[kk] == T;
+    unsigned eqm = __ballot_sync(0xffffffffu, iseq);
+    bool take = isgt || (iseq && eq_before + __popc(eqm & below) < need);
+    unsigned tm = __ballot_sync(0xffffffffu, take);
+    if (take) out[pos + __popc(tm & below)] = (int16_t)(lane + 32 * kk);
+    pos += __popc(tm);
+    eq_before += __popc(eqm);
+  }
+  __syncwarp();
+}
+
 // k rounds of warp argmax over the lane-held values val[kk] (atom lane + 32 kk, only
 // atoms < nvalid compete): largest |val| first, ties to the lower atom.  Writes the
 // chosen atoms to out[0..k).
@@ -207,51 +492,6 @@ __device__ void topk_atoms(Warp& w, const float (&val)[kNK], int nvalid, int k, 
     }
     if ((bn & 31) == w.lane) taken |= 1u << (bn >> 5);
     if (w.lane == 0) out[j] = (int16_t)bn;
-  }
-  __syncwarp();
-}
-
-// k rounds of warp argmax over FP64 values vals[0..cnt) keyed by atoms[0..cnt):
-// largest |value| first, ties to the lower atom.  Writes chosen positions to out.
-__device__ void topk_positions(Warp& w, const double* vals, const int16_t* atoms, int cnt, int k,
-                               int16_t* out) {
-  constexpr int kPK = kMaxN / 32;
-  double lv[kPK];
-  int la[kPK];
-#pragma unroll
-  for (int kk = 0; kk < kPK; ++kk) {
-    int j = w.lane + 32 * kk;
-    lv[kk] = j < cnt ? fabs(vals[j]) : -1.0;
-    la[kk] = j < cnt ? atoms[j] : (1 << 30);
-  }
-  unsigned taken = 0;
-  for (int j = 0; j < k; ++j) {
-    double bv = -2.0;
-    int ba = 1 << 30, bp = -1;
-#pragma unroll
-    for (int kk = 0; kk < kPK; ++kk) {
-      int pos = w.lane + 32 * kk;
-      if (pos < cnt && !((taken >> kk) & 1u)) {
-        if (lv[kk] > bv || (lv[kk] == bv && la[kk] < ba)) {
-          bv = lv[kk];
-          ba = la[kk];
-          bp = pos;
-        }
-      }
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      double ov = __shfl_xor_sync(0xffffffffu, bv, o);
-      int oa = __shfl_xor_sync(0xffffffffu, ba, o);
-      int op = __shfl_xor_sync(0xffffffffu, bp, o);
-      if (ov > bv || (ov == bv && oa < ba)) {
-        bv = ov;
-        ba = oa;
-        bp = op;
-      }
-    }
-    if ((bp & 31) == w.lane) taken |= 1u << (bp >> 5);
-    if (w.lane == 0) out[j] = (int16_t)bp;
   }
   __syncwarp();
 }
@@ -290,17 +530,38 @@ __device__ bool ls_fresh(Warp& w, const int16_t* atoms, int n, double* L, double
   return true;
 }
 
+template <int VR>
+__device__ bool ls_solve(Warp& w, const int16_t* atoms, int n, double* Lbuf, double* invdbuf,
+                         double* vbuf, double* s, int cap) {
+  fill_rhs(w, atoms, n, vbuf);
+  float* L32 = reinterpret_cast<float*>(Lbuf);
+  float* inv32 = reinterpret_cast<float*>(invdbuf);
+  if (chol32<VR>(w, L32, inv32, cap, n, atoms) && refine32<VR>(w, L32, inv32, cap, n, atoms, vbuf, s))
+    return true;
+  // FP64 fallback: in place when the shared regions are FP64-sized, else in the warp's
+  // global slot (capacity dmax >= n)
+  if (w.fb) {
+    const int D = w.p.dmax;
+    double* Lg = w.fb;
+    return ls_fresh(w, atoms, n, Lg, Lg + D * (D + 1) / 2, Lg + D * (D + 1) / 2 + D, s, D);
+  }
+  return ls_fresh(w, atoms, n, Lbuf, invdbuf, vbuf, s, cap);
+}
+
 // Minimum-norm solution for |c| > M: s = A_c^T H^{-1} y with H = A_c A_c^T (M x M).
 __device__ bool ls_min_norm(Warp& w, const int16_t* atoms, int n, double* s) {
   const int M = w.p.M;
   const double* At = w.p.At64;
-  double* L = w.L;
+  // FP64 M x M factor: the warp's global slot (dmax = M here), else the FP64-sized smem
+  double* L = w.fb ? w.fb : w.L;
+  double* invd = w.fb ? w.fb + M * (M + 1) / 2 : w.invd;
+  double* v = w.fb ? w.fb + M * (M + 1) / 2 + M : w.v;
   const int cap = M;
   bool ok = true;
   for (int k = 0; k < M; ++k) {
     // row k of H: H(k, t) = sum_j A[k][c_j] A[t][c_j]
     ok &= append_row(
-        w, L, w.invd, w.v, cap, k,
+        w, L, invd, v, cap, k,
         [&](int t) {
           double h = 0.0;
           for (int j = 0; j < n; ++j) {
@@ -313,7 +574,7 @@ __device__ bool ls_min_norm(Warp& w, const int16_t* atoms, int n, double* s) {
     if (!ok) return false;
   }
   double* zv = w.svals;  // z = H^{-1} y
-  back_solve(w, L, w.invd, w.v, zv, cap, M);
+  back_solve(w, L, invd, v, zv, cap, M);
   for (int j = w.lane; j < n; j += 32) {
     const double* a = At + (size_t)atoms[j] * M;
     double acc = 0.0;
@@ -324,15 +585,16 @@ __device__ bool ls_min_norm(Warp& w, const int16_t* atoms, int n, double* s) {
   return true;
 }
 
-template <int ALGO>
-__global__ void __launch_bounds__(256) k_greedy(GrParams p) {
+template <int ALGO, int VR>
+__global__ void __launch_bounds__(256, 2) k_greedy(GrParams p) {
   extern __shared__ __align__(16) unsigned char gsm[];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int M = p.M, N = p.N;
-  Layout lay(M, N, p.cmax, p.dmax, p.kmax);
+  Layout lay(M, N, p.cmax, p.dmax, p.kmax, p.fb64 == nullptr, ALGO == kGomp);
   unsigned char* base = gsm + (size_t)wid * p.warp_bytes;
   Warp w{p, lane};
   w.y = (float*)(base + lay.y);
+  w.rf = (float*)(base + lay.rf);
   w.r = (double*)(base + lay.r);
   w.xd = (float*)(base + lay.xd);
   w.b = (double*)(base + lay.b);
@@ -353,6 +615,7 @@ __global__ void __launch_bounds__(256) k_greedy(GrParams p) {
   w.q = (int16_t*)(base + lay.q);
   w.sel = (int16_t*)(base + lay.sel);
   w.tmp16 = (int16_t*)(base + lay.tmp16);
+  w.fb = p.fb64 ? p.fb64 + (size_t)(blockIdx.x * (blockDim.x >> 5) + wid) * p.fb_slot : nullptr;
 
   for (int n = lane; n < N; n += 32) {
     w.xd[n] = 0.f;
@@ -381,6 +644,7 @@ __global__ void __launch_bounds__(256) k_greedy(GrParams p) {
       bad |= !isfinite(yv);
       w.y[m] = yv;
       w.r[m] = (double)yv;  // r^0 = y
+      w.rf[m] = yv;
     }
     if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(p.status, kStNonFinite);
     __syncwarp();
@@ -393,8 +657,9 @@ __global__ void __launch_bounds__(256) k_greedy(GrParams p) {
       float val[kNK];
 #pragma unroll
       for (int kk = 0; kk < kNK; ++kk) val[kk] = 0.f;
+#pragma unroll 4
       for (int m = 0; m < M; ++m) {
-        float rm = (float)w.r[m];
+        float rm = w.rf[m];
         const float* arow = p.A32 + (size_t)m * N;
 #pragma unroll
         for (int kk = 0; kk < kNK; ++kk) {
@@ -410,72 +675,55 @@ __global__ void __launch_bounds__(256) k_greedy(GrParams p) {
         }
       }
       const int ksel = ALGO == kGomp ? G : (ALGO == kCosamp ? 2 * kappa : kappa);
-      topk_atoms(w, val, N, ksel, w.sel);
+      if (ksel > 8)
+        topk_select_atoms(w, val, N, ksel, w.sel);
+      else
+        topk_atoms(w, val, N, ksel, w.sel);
 
-      // ---- support c ----
-      int nc_old = nc;
-      if (ALGO == kGomp) {
-        // c = Theta U c, new atoms appended in selection order
-        for (int j = 0; j < ksel; ++j) {
-          int a = w.sel[j];
-          if (!w.inc[a]) {
-            __syncwarp();
-            if (lane == 0) {
-              w.inc[a] = 1;
-              w.c[nc] = (int16_t)a;
-            }
-            ++nc;
+      // ---- support c (kept sorted by atom) ----
+      if (ALGO == kBiht) {
+        // c = supp(x): the nonzero entries of the previous x, compacted by ballot
+        const unsigned below = (1u << lane) - 1u;
+        for (int n = lane; n < N; n += 32) w.inc[n] = 0;
+        __syncwarp();
+        int cnt = 0;
+        for (int base = 0; base < nq; base += 32) {
+          int j = base + lane;
+          bool nz = j < nq && w.xq[j] != 0.0;
+          unsigned m = __ballot_sync(0xffffffffu, nz);
+          if (nz) {
+            w.c[cnt + __popc(m & below)] = w.q[j];
+            w.inc[w.q[j]] = 1;
           }
-          __syncwarp();
+          cnt += __popc(m);
         }
-      } else {
-        // CoSaMP: c = Theta U c_prev (c_prev = last pruned support);
-        // BIHT: c = Theta U supp(x).  Both held sorted.
-        if (ALGO == kBiht) {
-          nc = 0;
-          for (int j = 0; j < nq; ++j)
-            if (w.xq[j] != 0.0) {
-              if (lane == 0) w.c[nc] = w.q[j];
-              ++nc;
-            }
-          __syncwarp();
-          for (int n = lane; n < N; n += 32) w.inc[n] = 0;
-          __syncwarp();
-          for (int j = lane; j < nc; j += 32) w.inc[w.c[j]] = 1;
-          __syncwarp();
-        }
-        for (int j = 0; j < ksel; ++j) {
-          int a = w.sel[j];
-          if (!w.inc[a]) {
-            __syncwarp();
-            if (lane == 0) {
-              w.inc[a] = 1;
-              w.c[nc] = (int16_t)a;
-            }
-            ++nc;
-          }
-          __syncwarp();
-        }
-        sort_atoms(w, w.c, nullptr, nc);
+        nc = cnt;
+        __syncwarp();
       }
+      // c = Theta U c (gOMP: the growing support; CoSaMP: the last pruned support)
+      {
+        const unsigned below = (1u << lane) - 1u;
+        for (int base = 0; base < ksel; base += 32) {
+          int j = base + lane;
+          int a = j < ksel ? w.sel[j] : 0;
+          bool isnew = j < ksel && !w.inc[a];
+          unsigned m = __ballot_sync(0xffffffffu, isnew);
+          if (isnew) {
+            w.c[nc + __popc(m & below)] = (int16_t)a;
+            w.inc[a] = 1;
+          }
+          nc += __popc(m);
+          __syncwarp();
+        }
+      }
+      sort_atoms(w, w.c, nullptr, nc);
 
       // ---- step 2: least squares on c ----
       if (nc > 0) {
-        if (ALGO == kGomp) {
-          const double* G64 = p.G64;
-          for (int k = nc_old; k < nc && !fail; ++k) {
-            const double* grow = G64 + (size_t)w.c[k] * N;
-            double bk = rhs(w, w.c[k]);
-            const int16_t* cc = w.c;
-            fail |= !append_row(w, w.L, w.invd, w.v, p.dmax, k, [&](int t) { return grow[cc[t]]; },
-                                bk);
-          }
-          if (!fail) back_solve(w, w.L, w.invd, w.v, w.s, p.dmax, nc);
-        } else if (nc <= M) {
-          fail |= !ls_fresh(w, w.c, nc, w.L, w.invd, w.v, w.s, p.dmax);
-        } else {
+        if (nc <= M)
+          fail |= !ls_solve<VR>(w, w.c, nc, w.L, w.invd, w.v, w.s, p.dmax);
+        else
           fail |= !ls_min_norm(w, w.c, nc, w.s);
-        }
       }
       if (fail) break;
 
@@ -485,7 +733,7 @@ __global__ void __launch_bounds__(256) k_greedy(GrParams p) {
       __syncwarp();
       int keep = nc < kappa ? nc : kappa;
       if (nc > kappa) {
-        topk_positions(w, w.s, w.c, nc, keep, w.sel);
+        topk_select_positions(w, w.s, nc, keep, w.sel);  // c sorted: positions order atoms
       } else {
         for (int j = lane; j < nc; j += 32) w.sel[j] = (int16_t)j;
         __syncwarp();
@@ -496,10 +744,9 @@ __global__ void __launch_bounds__(256) k_greedy(GrParams p) {
         w.xq[j] = w.s[pos];
       }
       __syncwarp();
-      nq = keep;
-      sort_atoms(w, w.q, w.xq, nq);
+      nq = keep;  // q inherits c's ascending order
       if (ALGO == kGomp && nq > 0) {
-        fail |= !ls_fresh(w, w.q, nq, w.Lq, w.invq, w.vq, w.sq, p.kmax);
+        fail |= !ls_solve<VR>(w, w.q, nq, w.Lq, w.invq, w.vq, w.sq, p.kmax);
         if (fail) break;
         for (int j = lane; j < nq; j += 32) w.xq[j] = w.sq[j];
         __syncwarp();
@@ -527,6 +774,7 @@ __global__ void __launch_bounds__(256) k_greedy(GrParams p) {
         double df = rn - w.r[m];
         d2 += df * df;
         w.r[m] = rn;
+        w.rf[m] = (float)rn;
       }
       d2 = warp_sum(d2);
       __syncwarp();
@@ -555,9 +803,18 @@ __global__ void __launch_bounds__(256) k_greedy(GrParams p) {
   }
 }
 
+// The kernel instance whose register-held vectors cover systems of up to 32 vr rows.
+template <int ALGO>
+auto greedy_kernel(int vr) {
+  if (vr <= 1) return k_greedy<ALGO, 1>;
+  if (vr == 2) return k_greedy<ALGO, 2>;
+  if (vr == 3) return k_greedy<ALGO, 3>;
+  return k_greedy<ALGO, 4>;
+}
+
 }  // namespace
 
-cudaError_t launch_greedy(const Ctx& c, GreedyAlgo algo, const GreedyArgs& a) {
+cudaError_t launch_greedy(Ctx& c, GreedyAlgo algo, const GreedyArgs& a) {
   if (a.P == 0) return cudaSuccess;
   GrParams p{};
   p.M = c.M;
@@ -599,12 +856,17 @@ cudaError_t launch_greedy(const Ctx& c, GreedyAlgo algo, const GreedyArgs& a) {
   p.cmax = cmax;
   p.dmax = cmax < M ? cmax : M;
   p.kmax = K > 0 ? K : 1;
-  Layout lay(M, N, p.cmax, p.dmax, p.kmax);
+  // FP32 factors in shared memory; the rare FP64 fallback (and the |c| > M minimum-norm
+  // solve) use one global slot per resident warp, so more warps fit on an SM.
+  Layout lay(M, N, p.cmax, p.dmax, p.kmax, false, algo == kGomp);
   p.warp_bytes = lay.total;
-  const int max_smem = 220 * 1024;
-  int warps = max_smem / lay.total;
-  if (warps > 8) warps = 8;
-  if (warps < 1) return cudaErrorInvalidConfiguration;
+  // one CTA of up to 8 warps per SM, or two smaller ones if that seats more warps
+  int warps1 = (220 * 1024) / lay.total, warps2 = (110 * 1024) / lay.total;
+  if (warps1 > 8) warps1 = 8;
+  if (warps2 > 8) warps2 = 8;
+  int warps = (warps2 >= 1 && 2 * warps2 >= warps1) ? warps2 : warps1;
+  if (warps < 1) warps = 1;
+  if ((size_t)warps * lay.total > 220 * 1024) return cudaErrorInvalidConfiguration;
   size_t smem = (size_t)warps * lay.total;
   cudaError_t e = cudaMemsetAsync(c.counter, 0, sizeof(unsigned long long), c.stream);
   if (e != cudaSuccess) return e;
@@ -616,12 +878,25 @@ cudaError_t launch_greedy(const Ctx& c, GreedyAlgo algo, const GreedyArgs& a) {
     long long grid = (long long)c.num_sms * per_sm;
     long long need = (a.P + warps - 1) / warps;
     if (grid > need) grid = need;
+    const int D = p.dmax;
+    p.fb_slot = D * (D + 1) / 2 + 2 * D;
+    size_t elems = (size_t)grid * warps * p.fb_slot;
+    if (c.fb64_elems < elems) {
+      cudaFree(c.fb64);
+      c.fb64 = nullptr;
+      c.fb64_elems = 0;
+      cudaError_t ea = cudaMalloc(reinterpret_cast<void**>(&c.fb64), sizeof(double) * elems);
+      if (ea != cudaSuccess) return ea;
+      c.fb64_elems = elems;
+    }
+    p.fb64 = c.fb64;
     kern<<<(unsigned)grid, warps * 32, smem, c.stream>>>(p);
     return cudaGetLastError();
   };
-  if (algo == kGomp) return launch(k_greedy<kGomp>);
-  if (algo == kBiht) return launch(k_greedy<kBiht>);
-  return launch(k_greedy<kCosamp>);
+  const int vr = (p.dmax + 31) / 32;
+  if (algo == kGomp) return launch(greedy_kernel<kGomp>(vr));
+  if (algo == kBiht) return launch(greedy_kernel<kBiht>(vr));
+  return launch(greedy_kernel<kCosamp>(vr));
 }
 
 }  // namespace cs
@@ -765,13 +1040,13 @@ cudaError_t launch_gomp_noalloc(const double* A64, int M, int N, const GreedyArg
   p.cmax = cmax;
   p.dmax = cmax < M ? cmax : M;
   p.kmax = K > 0 ? K : 1;
-  Layout wl(M, N, p.cmax, p.dmax, p.kmax);
+  Layout wl(M, N, p.cmax, p.dmax, p.kmax, true, true);
   p.warp_bytes = wl.total;
   int warps = (220 * 1024) / wl.total;
   if (warps > 8) warps = 8;
   if (warps < 1) return cudaErrorInvalidConfiguration;
   size_t smem = (size_t)warps * wl.total;
-  auto kern = k_greedy<kGomp>;
+  auto kern = greedy_kernel<kGomp>((p.dmax + 31) / 32);
   e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
