@@ -54,7 +54,9 @@ def config(extra=None):
                      f"measure + FISTA({ITERS}) + ADMM({ITERS}) + gOMP(k={KAPPA},G={G}) + "
                      f"BIHT(k={KAPPA}) + CoSaMP(k={KAPPA})",
          "pixels": P, "bands": N, "measurements": M, "algorithms": ALGOS,
-         "spectra_per_step": P * len(ALGOS), "precision": "fp32",
+         "spectra_per_step": P * len(ALGOS),
+         "precision": "FISTA split-BF16 tensor cores (mixed); ADMM FP32; greedy FP32 "
+                      "correlation + FP32 Cholesky with FP64 refinement",
          "l2": "flushed between timed steps (256 MiB write)"}
     if extra:
         c.update(extra)
@@ -241,6 +243,11 @@ def run_gpu(args):
     iters = {a: torch.zeros(P, device=dev, dtype=torch.int32) for a in ALGOS}
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     opts = {a: cs.make_opts(eps=EPS, max_iters=100, mu=MU, iters_out=iters[a]) for a in ALGOS}
+    # FISTA runs on the tensor cores (split-BF16, mixed precision); its plain FP32 run is
+    # timed beside it for the mixed-vs-FP32 comparison
+    opts["fista"] = cs.make_opts(eps=EPS, prec=cs.CS_BF16, iters_out=iters["fista"])
+    fista32_out = torch.empty((P, N), device=dev)
+    fista32_opts = cs.make_opts(eps=EPS)
 
     def step(ev=None):
         def mark(k):
@@ -286,6 +293,16 @@ def run_gpu(args):
     if dist:
         dist.barrier()
     cs.cs_sync(ctx)
+    # the FP32 FISTA kernel alone, same input, for the mixed-vs-FP32 comparison
+    f32_ms = []
+    for _ in range(2):
+        flush.fill_(1)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        cs.cs_recover_fista(ctx, Y, fista32_out, LAM, ITERS, fista32_opts)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        f32_ms.append(e0.elapsed_time(e1))
     t_step = sum(step_ms) / len(step_ms)
     if dist:
         tt = torch.tensor([t_step], device=dev)
@@ -305,7 +322,8 @@ def run_gpu(args):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         cs.cs_measure(ctx, Xh, Yh, Eh)
-        cs.cs_recover_fista(ctx, Yh, outh["fista"], LAM, ITERS, cs.make_opts(eps=EPS))
+        cs.cs_recover_fista(ctx, Yh, outh["fista"], LAM, ITERS,
+                            cs.make_opts(eps=EPS, prec=cs.CS_BF16))
         cs.cs_recover_admm(ctx, Yh, outh["admm"], RHO, LAM, ITERS, cs.make_opts(eps=EPS))
         cs.cs_recover_gomp(ctx, Yh, outh["gomp"], KAPPA, G, cs.make_opts(eps=EPS))
         cs.cs_recover_biht(ctx, Yh, outh["biht"], KAPPA, cs.make_opts(eps=EPS, mu=MU))
@@ -355,6 +373,14 @@ def run_gpu(args):
             g = outs[a][:n_s].double().cpu().numpy()
             r = ref[a] if a in ("fista", "admm") else ref[a][0]
             acc[a] = float(np.linalg.norm(g - r) / np.linalg.norm(r))
+        g32 = fista32_out[:n_s].double().cpu().numpy()
+        acc["fista_fp32"] = float(np.linalg.norm(g32 - ref["fista"]) / np.linalg.norm(ref["fista"]))
+        f32 = sum(f32_ms) / len(f32_ms)
+        kernels["fista_fp32"] = {"ms": f32, "tflops": flops["fista"] / (f32 * 1e-3) / 1e12,
+                                 "frac_fp32_peak": flops["fista"] / (f32 * 1e-3) / 1e12 /
+                                 FP32_PEAK_TFLOPS}
+        kernels["fista"]["precision"] = "split-BF16 tcgen05 (3 MMAs per product), FP32 acc"
+        kernels["fista"]["speedup_vs_fp32"] = f32 / kern_ms["fista"]
         cpu_value = n_s * len(ALGOS) / secs
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_step,

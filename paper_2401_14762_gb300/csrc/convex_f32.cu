@@ -494,6 +494,7 @@ cudaError_t admm_mr(const Ctx& c, CvParams p, int64_t blocks) {
   } while (0)
 
 cudaError_t launch_fista(const Ctx& c, const ConvexArgs& a) {
+  if (a.prec != CS_FP32 && fista_tc_supported(c.M, c.N)) return launch_fista_tc(c, a);
   CvParams p = base_params(c);
   p.Y = a.Y;
   p.X = a.X;

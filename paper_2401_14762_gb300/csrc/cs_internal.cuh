@@ -77,6 +77,8 @@ struct ConvexArgs {
   cs_precision prec;
 };
 cudaError_t launch_fista(const Ctx& c, const ConvexArgs& a);
+bool fista_tc_supported(int M, int N);
+cudaError_t launch_fista_tc(const Ctx& c, const ConvexArgs& a);
 cudaError_t launch_admm(const Ctx& c, const ConvexArgs& a);
 
 // ---- greedy (gOMP / BIHT / CoSaMP) ----

@@ -5,20 +5,21 @@
 // once.  Per iteration the warp
 //   1. correlates: p = A^T r (FP32, lane l owns atoms l, l+32, ...), for BIHT
 //      u = x + mu p,
-//   2. selects the G / 2 kappa / kappa largest magnitudes with warp argmax rounds
-//      (ties to the lower atom index),
-//   3. forms the support c (union of Theta with c or supp(x)),
-//   4. solves min ||A_c s - y|| through the normal equations G_c s = (A^T y)_c in FP64:
-//      G_c comes from the precomputed FP64 Gram matrix A^T A and is factored row by
-//      row (G_c = L L^T, the next row from a forward substitution), so gOMP, whose
-//      support only grows, extends its factor instead of refactoring; when |c| > M the
-//      minimum-norm solution s = A_c^T (A_c A_c^T)^{-1} y is used instead,
+//   2. selects the G / 2 kappa / kappa largest magnitudes (ties to the lower atom):
+//      warp argmax rounds for small k, a 32-step radix search on the magnitude bits for
+//      large k,
+//   3. forms the support c (union of Theta with c or supp(x)), kept sorted by atom,
+//   4. solves min ||A_c s - y|| through the normal equations G_c s = (A^T y)_c: G_c is
+//      gathered from the precomputed FP64 Gram matrix A^T A, factored in FP32, and the
+//      solution is refined to FP64 accuracy with FP64 residuals (an FP64 factorisation
+//      is the fallback); when |c| > M the minimum-norm solution s = A_c^T (A_c A_c^T)^{-1} y
+//      is used instead,
 //   5. prunes to kappa atoms (and, for gOMP, refits on them),
 //   6. recomputes the residual r = y - A x and Delta = ||r - r_prev|| in FP64 (the
 //      paper's absolute eps = 1e-8 lies below FP32 resolution of r).
-// Supports are kept sorted by atom index (gOMP's growing c in insertion order), so an
-// unchanged support reproduces x bit for bit and Delta = 0 exactly, as in the paper's
-// stopping rule.  All per-pixel state sits in the warp's slice of shared memory.
+// Because supports are sorted and every step is deterministic, an unchanged support
+// reproduces x bit for bit and Delta = 0 exactly, as in the paper's stopping rule.  All
+// per-pixel state sits in the warp's slice of shared memory.
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -463,18 +464,18 @@ __device__ void topk_select_positions(Warp& w, const double* vals, int cnt, int 
 }
 
 // k rounds of warp argmax over the lane-held values val[kk] (atom lane + 32 kk, only
-// atoms < nvalid compete): largest |val| first, ties to the lower atom.  Writes the
-// chosen atoms to out[0..k).
+// atoms < nvalid compete): largest |val| first, ties to the lower atom; NaN ranks below
+// every number, so k distinct atoms are always chosen.  Writes them to out[0..k).
 __device__ void topk_atoms(Warp& w, const float (&val)[kNK], int nvalid, int k, int16_t* out) {
   unsigned taken = 0;
   for (int j = 0; j < k; ++j) {
-    float bv = -1.f;
+    float bv = -2.f;
     int bn = 1 << 30;
 #pragma unroll
     for (int kk = 0; kk < kNK; ++kk) {
       int n = w.lane + 32 * kk;
       if (n < nvalid && !((taken >> kk) & 1u)) {
-        float a = fabsf(val[kk]);
+        float a = isnan(val[kk]) ? -1.f : fabsf(val[kk]);
         if (a > bv || (a == bv && n < bn)) {
           bv = a;
           bn = n;
@@ -496,13 +497,14 @@ __device__ void topk_atoms(Warp& w, const float (&val)[kNK], int nvalid, int k, 
   __syncwarp();
 }
 
-// Sorts atoms[0..n) ascending (distinct keys) by rank, carrying FP64 values if given.
+// Sorts atoms[0..n) ascending by rank (equal keys keep their order, so every rank is
+// written even if a key repeats), carrying FP64 values if given.
 __device__ void sort_atoms(Warp& w, int16_t* atoms, double* vals, int n) {
   int16_t* tmp = w.tmp16;
   double* tv = w.wv;
   for (int j = w.lane; j < n; j += 32) {
     int a = atoms[j], rank = 0;
-    for (int t = 0; t < n; ++t) rank += atoms[t] < a;
+    for (int t = 0; t < n; ++t) rank += atoms[t] < a || (atoms[t] == a && t < j);
     tmp[rank] = (int16_t)a;
     if (vals) tv[rank] = vals[j];
   }

@@ -17,10 +17,10 @@ MARGIN_FP32 = 1e-3
 U32 = 2.0 ** -24  # FP32 unit roundoff
 
 
-def support(X):
-    """Support of each row: {j : |x_j| > 1e-6 max|x|} (entries at rounding level excluded)."""
+def support(X, rel=1e-6):
+    """Support of each row: {j : |x_j| > rel max|x|} (entries at rounding level excluded)."""
     X = np.abs(np.asarray(X, np.float64))
-    return X > 1e-6 * X.max(axis=1, keepdims=True)
+    return X > rel * X.max(axis=1, keepdims=True)
 
 
 def iterate_conditioning(run, Y, rel=1e-7, seed=0):

@@ -65,7 +65,8 @@ def test_measure(cs, M, N):
     E = sy.noise(P, M, 1e-3, 3).astype(np.float32)
     ctx = cs.cs_create(M, N, Phi=Phi)
     Yd = torch.zeros((P, M), device="cuda")
-    cs.cs_measure(ctx, torch.from_numpy(X).cuda(), Yd, torch.from_numpy(E).cuda())
+    Xd, Ed = torch.from_numpy(X).cuda(), torch.from_numpy(E).cuda()  # alive until the sync
+    cs.cs_measure(ctx, Xd, Yd, Ed)
     cs.cs_sync(ctx)
     ref = orc.measure(A, X.astype(np.float64), E.astype(np.float64))
     scale = np.linalg.norm(ref, axis=1, keepdims=True)
@@ -276,7 +277,8 @@ def test_nonfinite_input_is_reported(cs, small):
     Y = small.Y[:8].copy()
     Y[2, 5] = np.nan
     X = torch.zeros((8, small.N), device="cuda")
-    cs.cs_recover_gomp(ctx, torch.from_numpy(Y).cuda(), X, 8, 2)
+    Yd = torch.from_numpy(Y).cuda()  # kept alive until the asynchronous call is synced
+    cs.cs_recover_gomp(ctx, Yd, X, 8, 2)
     with pytest.raises(cs.CsError) as e:
         cs.cs_sync(ctx)
     assert e.value.status == cs.CS_ERR_NONFINITE
