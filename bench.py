@@ -249,6 +249,8 @@ def run_gpu(args):
     fista32_out = torch.empty((P, N), device=dev)
     fista32_opts = cs.make_opts(eps=EPS)
 
+    work = {}
+
     def step(ev=None):
         def mark(k):
             if ev is not None:
@@ -262,10 +264,16 @@ def run_gpu(args):
         mark("admm")
         cs.cs_recover_gomp(ctx, Y, outs["gomp"], KAPPA, G, opts["gomp"])
         mark("gomp")
+        if ev is None:
+            work["gomp"] = cs.cs_get_work(ctx)
         cs.cs_recover_biht(ctx, Y, outs["biht"], KAPPA, opts["biht"])
         mark("biht")
+        if ev is None:
+            work["biht"] = cs.cs_get_work(ctx)
         cs.cs_recover_cosamp(ctx, Y, outs["cosamp"], KAPPA, opts["cosamp"])
         mark("cosamp")
+        if ev is None:
+            work["cosamp"] = cs.cs_get_work(ctx)
 
     for _ in range(args.warmup):
         step()
@@ -340,19 +348,16 @@ def run_gpu(args):
         flops = {"fista": 4.0 * M * N * its["fista"],
                  "admm": (4.0 * M * N + 2.0 * M * M) * its["admm"],
                  "measure": 2.0 * M * N * P}
+        flops.update(work)  # greedy: algorithmic flops counted by the kernels (warm-up run)
         dom = max(kern_ms, key=kern_ms.get)
         pk = peaks()
-        roof = None
-        if dom in flops:
-            ach = flops[dom] / (kern_ms[dom] * 1e-3) / 1e12
-            roof = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": FP32_PEAK_TFLOPS,
-                    "unit": "TFLOP/s", "frac": ach / FP32_PEAK_TFLOPS,
-                    "traffic": measured_traffic(dom),
-                    "peak_kind": "derived FP32 FMA peak: 152 SMs x 128 lanes x 2 x 2070 MHz"}
-        else:
-            roof = {"kernel": dom, "bound": "alu", "achieved": None, "peak": FP64_PEAK_TFLOPS,
-                    "unit": "TFLOP/s", "frac": None, "traffic": measured_traffic(dom),
-                    "peak_kind": "FP64 nominal"}
+        ach = flops[dom] / (kern_ms[dom] * 1e-3) / 1e12
+        roof = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": FP32_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "frac": ach / FP32_PEAK_TFLOPS,
+                "traffic": measured_traffic(dom),
+                "peak_kind": "derived FP32 FMA peak: 152 SMs x 128 lanes x 2 x 2070 MHz",
+                "work": "algorithmic flops of the method (correlation, Cholesky least squares "
+                        "per support, residual) counted by the kernel"}
         kernels = {}
         for k, ms in kern_ms.items():
             ent = {"ms": ms, "share": ms / t_step}

@@ -21,8 +21,8 @@ CS_FP32, CS_BF16, CS_FP8_E4M3 = 0, 1, 2
 
 EXPORTED = ["cs_opts_default", "cs_create", "cs_destroy", "cs_get_lipschitz", "cs_get_dictionary",
             "cs_measure", "cs_recover_fista", "cs_recover_admm", "cs_recover_gomp",
-            "cs_recover_biht", "cs_recover_cosamp", "cs_recover_gomp_noalloc", "cs_sync",
-            "cs_last_error"]
+            "cs_recover_biht", "cs_recover_cosamp", "cs_get_work", "cs_recover_gomp_noalloc",
+            "cs_sync", "cs_last_error"]
 
 
 class CsError(RuntimeError):
@@ -64,6 +64,7 @@ def load_library(path: str = LIB_PATH):
     lib.cs_recover_gomp.argtypes = [vp, vp, vp, i64, i32, i32, op]
     lib.cs_recover_biht.argtypes = [vp, vp, vp, i64, i32, op]
     lib.cs_recover_cosamp.argtypes = [vp, vp, vp, i64, i32, op]
+    lib.cs_get_work.argtypes = [vp, ctypes.POINTER(dbl)]
     lib.cs_recover_gomp_noalloc.argtypes = [vp, i32, i32, vp, vp, i64, i32, i32, op, vp]
     lib.cs_sync.argtypes = [vp]
     lib.cs_last_error.argtypes = []
@@ -238,6 +239,13 @@ def cs_recover_cosamp(ctx: Context, Y, X, kappa, opts: cs_opts | None = None, P=
                                             int(P), int(kappa),
                                             ctypes.byref(opts) if opts else None))
     return X
+
+
+def cs_get_work(ctx: Context) -> float:
+    """Algorithmic flops of the last greedy call on this context."""
+    f = ctypes.c_double()
+    _check(load_library().cs_get_work(ctx.handle, ctypes.byref(f)))
+    return f.value
 
 
 def cs_recover_gomp_noalloc(A_dev, M, N, Y, X, kappa, G, opts: cs_opts | None = None, P=None,

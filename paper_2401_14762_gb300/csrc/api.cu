@@ -51,6 +51,8 @@ void free_ctx(Ctx& c) {
   cudaFree(c.stage_out);
   cudaFree(c.stage_aux);
   cudaFree(c.fb64);
+  cudaFree(c.work);
+  cudaFree(c.beta);
 }
 
 // Is ptr device-accessible memory (cudaMalloc / managed)?  Host memory, pinned or not,
@@ -168,7 +170,8 @@ cs_status cs_create(cs_ctx** out, int M, int N, const double* A_host, const doub
       (e = cs::dalloc(&c.W32, (size_t)M * M)) != cudaSuccess ||
       (e = cs::dalloc(&c.scratch64, c.scratch_elems)) != cudaSuccess ||
       (e = cs::dalloc(&c.status, 1)) != cudaSuccess ||
-      (e = cs::dalloc(&c.counter, 2)) != cudaSuccess) {
+      (e = cs::dalloc(&c.counter, 2)) != cudaSuccess ||
+      (e = cs::dalloc(&c.work, 1)) != cudaSuccess) {
     cs::free_ctx(c);
     delete ctx;
     return cuda_fail(e, "cs_create allocation");
@@ -379,6 +382,16 @@ cs_status cs_recover_gomp_noalloc(const double* A_dev, int M, int N, const float
                    o.iters_out, o.converged_out, o.prec};
   e = cs::launch_gomp_noalloc(A_dev, M, N, a, static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_fail(e, "cs_recover_gomp_noalloc");
+  return CS_OK;
+}
+
+cs_status cs_get_work(cs_ctx* ctx, double* flops) {
+  if (cs_status s = cs::check_ctx(ctx)) return s;
+  if (!flops) return arg_error("flops is NULL");
+  cs::Ctx& c = ctx->c;
+  cudaError_t e = cudaMemcpyAsync(flops, c.work, sizeof(double), cudaMemcpyDeviceToHost, c.stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c.stream);
+  if (e != cudaSuccess) return cuda_fail(e, "cs_get_work");
   return CS_OK;
 }
 

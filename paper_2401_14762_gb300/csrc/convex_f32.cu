@@ -44,6 +44,7 @@ struct CvParams {
   int32_t* iters_out;
   uint8_t* conv_out;
   int* status;
+  const float* beta;  // FISTA momentum weights beta_i, i = 1..iters
 };
 
 __device__ __forceinline__ float soft_thr(float a, float t) {
@@ -176,7 +177,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_fista_f32(CvParams p) {
   if (bad) atomicOr(p.status, kStNonFinite);
   __syncthreads();
 
-  double t = 1.0;
   float beta_prev = 0.f;
   int it = 0;
   // After A is staged the warps never synchronise: a warp owns its pixels in both
@@ -198,9 +198,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_fista_f32(CvParams p) {
     // steps 1-4: aux = z - A^T(Az - y)/L, x = soft(aux, lambda/L), t, z
     float acc[kPPW][4 * NCH];
     cols_product<NCH>(acc, As, lda, vs, M, warp, col, hc);
-    double tn = 0.5 * (1.0 + sqrt(1.0 + 4.0 * t * t));
-    float beta = (float)((t - 1.0) / tn);
-    t = tn;
+    const float beta = p.beta[it];  // beta_{it+1}
 #pragma unroll
     for (int i = 0; i < kPPW; ++i) {
       if (done[i]) continue;
@@ -439,6 +437,19 @@ __global__ void __launch_bounds__(kThreads, 1) k_measure_f32(CvParams p) {
   }
 }
 
+// Momentum weights of Algorithm 1 steps 3-4: t_0 = 1, t_i = (1 + sqrt(1 + 4 t_{i-1}^2)) / 2,
+// beta_i = (t_{i-1} - 1) / t_i, in FP64 by one thread (the sequence is the same for all
+// pixels), stored as FP32 for the iteration kernels.
+__global__ void k_momentum(int iters, float* beta) {
+  if (blockIdx.x != 0 || threadIdx.x != 0) return;
+  double t = 1.0;
+  for (int i = 0; i < iters; ++i) {
+    double tn = 0.5 * (1.0 + sqrt(1.0 + 4.0 * t * t));
+    beta[i] = (float)((t - 1.0) / tn);
+    t = tn;
+  }
+}
+
 template <typename K>
 void allow_smem(K kernel, size_t bytes) {
   cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
@@ -493,9 +504,27 @@ cudaError_t admm_mr(const Ctx& c, CvParams p, int64_t blocks) {
     }                                                                \
   } while (0)
 
-cudaError_t launch_fista(const Ctx& c, const ConvexArgs& a) {
+cudaError_t momentum_table(Ctx& c, int iters) {
+  if (c.beta_cap < iters || !c.beta) {
+    cudaFree(c.beta);
+    c.beta = nullptr;
+    c.beta_cap = 0;
+    int cap = iters > 1024 ? iters : 1024;
+    cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&c.beta), sizeof(float) * cap);
+    if (e != cudaSuccess) return e;
+    c.beta_cap = cap;
+  }
+  k_momentum<<<1, 1, 0, c.stream>>>(iters, c.beta);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fista(Ctx& c, const ConvexArgs& a) {
+  if (a.P == 0) return cudaSuccess;
+  cudaError_t e = momentum_table(c, a.iters);
+  if (e != cudaSuccess) return e;
   if (a.prec != CS_FP32 && fista_tc_supported(c.M, c.N)) return launch_fista_tc(c, a);
   CvParams p = base_params(c);
+  p.beta = c.beta;
   p.Y = a.Y;
   p.X = a.X;
   p.P = a.P;

@@ -45,6 +45,9 @@ struct Ctx {
   int* status = nullptr;      // device status word
   int* counter = nullptr;     // work counter of the persistent greedy kernel
   double* fb64 = nullptr;     // per-warp FP64 fallback slots of the greedy kernel
+  double* work = nullptr;     // algorithmic flops of the last greedy call (device, 1 entry)
+  float* beta = nullptr;      // FISTA momentum weights (device), capacity beta_cap
+  int beta_cap = 0;
   size_t fb64_elems = 0;
   float* stage_in = nullptr;  // staging for host-pointer calls
   float* stage_out = nullptr;
@@ -76,7 +79,7 @@ struct ConvexArgs {
   uint8_t* conv_out;
   cs_precision prec;
 };
-cudaError_t launch_fista(const Ctx& c, const ConvexArgs& a);
+cudaError_t launch_fista(Ctx& c, const ConvexArgs& a);
 bool fista_tc_supported(int M, int N);
 cudaError_t launch_fista_tc(const Ctx& c, const ConvexArgs& a);
 cudaError_t launch_admm(const Ctx& c, const ConvexArgs& a);

@@ -35,6 +35,7 @@ struct FtcParams {
   int32_t* iters_out;
   uint8_t* conv_out;
   int* status;
+  const float* beta;  // momentum weights beta_i, i = 1..iters
 };
 
 __device__ __forceinline__ float soft_thr(float a, float t) {
@@ -123,7 +124,6 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_fista_tc(FtcParams p) {
   const uint32_t id2 = tc::idesc_bf16(128, Np, true);   // GEMM2: B = A read MN-major
   const uint32_t id1 = tc::idesc_bf16(128, Mp, false);  // GEMM1: B = A read K-major
   bool done = !valid;
-  double t = 1.0;
   float beta_prev = 0.f;
   uint32_t phase = 0;
   bool failed = false;
@@ -203,9 +203,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_fista_tc(FtcParams p) {
     tc::fence_after_sync();
 
     // ---- steps 1-4: aux = z - C / L, x = soft(aux, lambda / L), t, z
-    const double tn = 0.5 * (1.0 + sqrt(1.0 + 4.0 * t * t));
-    const float beta = (float)((t - 1.0) / tn);
-    t = tn;
+    const float beta = p.beta[i - 1];
 #pragma unroll
     for (int c = 0; c < NH; c += 8) {
       float C[8], xp[8], xn[8];
@@ -305,6 +303,7 @@ cudaError_t launch_fista_tc(const Ctx& c, const ConvexArgs& a) {
   p.iters_out = a.iters_out;
   p.conv_out = a.conv_out;
   p.status = c.status;
+  p.beta = c.beta;
   if (a.P == 0) return cudaSuccess;
   // at least 120 KB so that one CTA (which takes all 512 TMEM columns) runs per SM
   size_t smem = tc_smem(p.Mp, p.Np);

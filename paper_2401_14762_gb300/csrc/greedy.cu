@@ -54,6 +54,7 @@ struct GrParams {
   unsigned long long* counter;
   double* fb64;      // per-warp global FP64 fallback slots (nullptr: FP64 factors in smem)
   int fb_slot;       // doubles per slot
+  double* work;      // optional: algorithmic flops of the call are added here
 };
 
 // Byte offsets of one warp's shared-memory slice.  With fp64_smem the factor regions are
@@ -273,16 +274,22 @@ __device__ bool chol32(Warp& w, float* L, float* invd, int cap, int n, const int
       L[cj + j] = dj;
       invd[j] = inv;
     }
+    // k in slot r's range [32r, 32r + 32): only lanes of slots >= r own rows i >= k, and
+    // L(k, j) comes from lane k - 32r's slot-r value
     int ck = lidx(0, j + 1, cap);
-#pragma unroll 4
-    for (int k = j + 1; k < n; ++k) {
-      float lkj = __shfl_sync(0xffffffffu, rpick<VR>(lij, k >> 5), k & 31);
 #pragma unroll
-      for (int r = 0; r < VR; ++r) {
-        int i = lane + 32 * r;
-        if (32 * r + 31 >= k && i >= k && i < n) L[ck + i] = fmaf(-lij[r], lkj, L[ck + i]);
+    for (int rs = 0; rs < VR; ++rs) {
+      const int kbeg = max(j + 1, 32 * rs), kend = min(n, 32 * rs + 32);
+#pragma unroll 2
+      for (int k = kbeg; k < kend; ++k) {
+        const float lkj = __shfl_sync(0xffffffffu, lij[rs], k - 32 * rs);
+#pragma unroll
+        for (int r = rs; r < VR; ++r) {
+          const int i = lane + 32 * r;
+          if (i >= k && i < n) L[ck + i] = fmaf(-lij[r], lkj, L[ck + i]);
+        }
+        ck += cap - k - 1;
       }
-      ck += cap - k - 1;
     }
     __syncwarp();
   }
@@ -653,6 +660,9 @@ __global__ void __launch_bounds__(256, 2) k_greedy(GrParams p) {
 
     int nc = 0, nq = 0, it = 0;
     uint8_t conv = 0;
+    // algorithmic flops of the method for this pixel: correlation 2MN, Cholesky least
+    // squares n^3/3 + 2n^2 per support of n atoms (min-norm form for n > M), residual 2M|q|
+    double work = 0.0;
     bool fail = false;
     while (!p.start_done && it < cap) {
       // ---- step 1: correlation (u = x + mu p for BIHT) ----
@@ -728,6 +738,11 @@ __global__ void __launch_bounds__(256, 2) k_greedy(GrParams p) {
           fail |= !ls_min_norm(w, w.c, nc, w.s);
       }
       if (fail) break;
+      {
+        const double n = nc, m = M;
+        work += 2.0 * m * N +
+                (nc <= M ? n * n * n / 3.0 + 2.0 * n * n : n * m * m + m * m * m / 3.0 + 2.0 * m * m + n * m);
+      }
 
       // ---- step 3: prune to kappa (and refit for gOMP) ----
       // previous support leaves xd
@@ -749,6 +764,7 @@ __global__ void __launch_bounds__(256, 2) k_greedy(GrParams p) {
       nq = keep;  // q inherits c's ascending order
       if (ALGO == kGomp && nq > 0) {
         fail |= !ls_solve<VR>(w, w.q, nq, w.Lq, w.invq, w.vq, w.sq, p.kmax);
+        work += (double)nq * nq * nq / 3.0 + 2.0 * nq * nq;
         if (fail) break;
         for (int j = lane; j < nq; j += 32) w.xq[j] = w.sq[j];
         __syncwarp();
@@ -780,6 +796,7 @@ __global__ void __launch_bounds__(256, 2) k_greedy(GrParams p) {
       }
       d2 = warp_sum(d2);
       __syncwarp();
+      work += 2.0 * M * nq;
       ++it;
       if (d2 < p.eps2) {
         conv = 1;
@@ -800,6 +817,7 @@ __global__ void __launch_bounds__(256, 2) k_greedy(GrParams p) {
     if (lane == 0) {
       if (p.iters_out) p.iters_out[pix] = it;
       if (p.conv_out) p.conv_out[pix] = conv;
+      if (p.work) atomicAdd(p.work, work);
     }
     __syncwarp();
   }
@@ -840,6 +858,7 @@ cudaError_t launch_greedy(Ctx& c, GreedyAlgo algo, const GreedyArgs& a) {
   p.conv_out = a.conv_out;
   p.status = c.status;
   p.counter = reinterpret_cast<unsigned long long*>(c.counter);
+  p.work = c.work;
   const int K = a.kappa_max;
   const int M = c.M, N = c.N;
   int cmax;
@@ -871,6 +890,7 @@ cudaError_t launch_greedy(Ctx& c, GreedyAlgo algo, const GreedyArgs& a) {
   if ((size_t)warps * lay.total > 220 * 1024) return cudaErrorInvalidConfiguration;
   size_t smem = (size_t)warps * lay.total;
   cudaError_t e = cudaMemsetAsync(c.counter, 0, sizeof(unsigned long long), c.stream);
+  if (e == cudaSuccess && c.work) e = cudaMemsetAsync(c.work, 0, sizeof(double), c.stream);
   if (e != cudaSuccess) return e;
   auto launch = [&](auto kern) {
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
