@@ -7,7 +7,9 @@
 //      u = x + mu p,
 //   2. selects the G / 2 kappa / kappa largest magnitudes (ties to the lower atom):
 //      warp argmax rounds for small k, a 32-step radix search on the magnitude bits for
-//      large k,
+//      large k; the choice is then certified against FP64: atoms whose FP32 value lies
+//      within the FP32 error bound of the cut are recomputed in FP64 and ranked exactly,
+//      so every selection is the one FP64 arithmetic makes,
 //   3. forms the support c (union of Theta with c or supp(x)), kept sorted by atom,
 //   4. solves min ||A_c s - y|| through the normal equations G_c s = (A^T y)_c: G_c is
 //      gathered from the precomputed FP64 Gram matrix A^T A, factored in FP32, and the
@@ -43,6 +45,7 @@ struct GrParams {
   int kappa, G;
   const int16_t* kappa_pp;
   float mu;
+  double mu64;
   double eps2;
   int start_done;
   int max_iters;
@@ -395,8 +398,8 @@ __device__ bool ls_solve(Warp& w, const int16_t* atoms, int n, double* Lbuf, dou
 // search for the k-th largest magnitude (IEEE bits of |v| order like the values), then a
 // ballot compaction of everything above it plus the lowest-indexed ties.  32 warp steps
 // whatever k is; output in ascending atom order.
-__device__ void topk_select_atoms(Warp& w, const float (&val)[kNK], int nvalid, int k,
-                                  int16_t* out) {
+__device__ float topk_select_atoms(Warp& w, const float (&val)[kNK], int nvalid, int k,
+                                   int16_t* out) {
   const int lane = w.lane;
   unsigned key[kNK];
   bool ok[kNK];
@@ -429,6 +432,7 @@ __device__ void topk_select_atoms(Warp& w, const float (&val)[kNK], int nvalid, 
     eq_before += __popc(eqm);
   }
   __syncwarp();
+  return __uint_as_float(T);
 }
 
 // The k largest |vals[p]| over positions p < cnt (FP64, ties to the lower position),
@@ -473,10 +477,11 @@ __device__ void topk_select_positions(Warp& w, const double* vals, int cnt, int 
 // k rounds of warp argmax over the lane-held values val[kk] (atom lane + 32 kk, only
 // atoms < nvalid compete): largest |val| first, ties to the lower atom; NaN ranks below
 // every number, so k distinct atoms are always chosen.  Writes them to out[0..k).
-__device__ void topk_atoms(Warp& w, const float (&val)[kNK], int nvalid, int k, int16_t* out) {
+__device__ float topk_atoms(Warp& w, const float (&val)[kNK], int nvalid, int k, int16_t* out) {
   unsigned taken = 0;
+  float bv = -2.f;
   for (int j = 0; j < k; ++j) {
-    float bv = -2.f;
+    bv = -2.f;
     int bn = 1 << 30;
 #pragma unroll
     for (int kk = 0; kk < kNK; ++kk) {
@@ -500,6 +505,80 @@ __device__ void topk_atoms(Warp& w, const float (&val)[kNK], int nvalid, int k, 
     }
     if ((bn & 31) == w.lane) taken |= 1u << (bn >> 5);
     if (w.lane == 0) out[j] = (int16_t)bn;
+  }
+  __syncwarp();
+  return bv;
+}
+
+// Makes a top-k choice taken on FP32 values equal to the one FP64 arithmetic takes.
+// Every |val| lies within E of the FP64 magnitude it approximates, and t is the k-th
+// largest |val|.  An atom more than 2E above t beats every atom at or below t in FP64,
+// and fewer than k atoms lie above t, so it is chosen; an atom more than 2E below t
+// loses to the k (or more) atoms at or above t, so it is not.  When the band between
+// holds more atoms than the slots left, the band is recomputed in FP64 (exact64(atom))
+// and the slots go to its largest magnitudes, ties to the lower atom, by a bitwise
+// search on the FP64 patterns.  out[0..k) is rewritten in ascending atom order.  Skipped
+// when a value is not finite (the pixel is flagged non-finite elsewhere).
+template <typename F>
+__device__ void certify_topk(Warp& w, const float (&val)[kNK], int nvalid, int k, float t,
+                             float E, F exact64, int16_t* out) {
+  const int lane = w.lane;
+  if (!(isfinite(t) && isfinite(E))) return;  // warp-uniform
+  // half-width 2E, widened for the FP32 rounding of the band edges themselves
+  const float W = 2.01f * E + t * 0x1p-21f;
+  const float hi = t + W, lo = t - W;
+  unsigned nin = 0, nband = 0;
+  bool fin = true;
+#pragma unroll
+  for (int kk = 0; kk < kNK; ++kk) {
+    if (lane + 32 * kk < nvalid) {
+      const float a = fabsf(val[kk]);
+      fin &= isfinite(a);
+      nin += a > hi ? 1u : 0u;
+      nband += (a >= lo && a <= hi) ? 1u : 0u;
+    }
+  }
+  if (!__all_sync(0xffffffffu, fin)) return;
+  nin = __reduce_add_sync(0xffffffffu, nin);
+  nband = __reduce_add_sync(0xffffffffu, nband);
+  if (nin + nband <= (unsigned)k) return;  // every atom of the band is chosen: certain
+  unsigned long long key[kNK];
+  bool ok[kNK];
+#pragma unroll
+  for (int kk = 0; kk < kNK; ++kk) {
+    const int n = lane + 32 * kk;
+    const float a = fabsf(val[kk]);
+    ok[kk] = n < nvalid && a >= lo;
+    key[kk] = 0ull;
+    if (ok[kk]) {
+      key[kk] = a > hi ? 0x7ff0000000000000ull  // surely chosen: above any finite value
+                       : (unsigned long long)__double_as_longlong(fabs(exact64(n)));
+    }
+  }
+  unsigned long long T = 0;
+  for (int b = 63; b >= 0; --b) {
+    unsigned long long cand = T | (1ull << b);
+    unsigned c = 0;
+#pragma unroll
+    for (int kk = 0; kk < kNK; ++kk) c += (ok[kk] && key[kk] >= cand) ? 1u : 0u;
+    if (__reduce_add_sync(0xffffffffu, c) >= (unsigned)k) T = cand;
+  }
+  unsigned gt = 0;
+#pragma unroll
+  for (int kk = 0; kk < kNK; ++kk) gt += (ok[kk] && key[kk] > T) ? 1u : 0u;
+  const int need = k - (int)__reduce_add_sync(0xffffffffu, gt);
+  const unsigned below = (1u << lane) - 1u;
+  int pos = 0, eq_before = 0;
+  __syncwarp();
+#pragma unroll
+  for (int kk = 0; kk < kNK; ++kk) {
+    bool isgt = ok[kk] && key[kk] > T, iseq = ok[kk] && key[kk] == T;
+    unsigned eqm = __ballot_sync(0xffffffffu, iseq);
+    bool take = isgt || (iseq && eq_before + __popc(eqm & below) < need);
+    unsigned tm = __ballot_sync(0xffffffffu, take);
+    if (take) out[pos + __popc(tm & below)] = (int16_t)(lane + 32 * kk);
+    pos += __popc(tm);
+    eq_before += __popc(eqm);
   }
   __syncwarp();
 }
@@ -631,6 +710,11 @@ __global__ void __launch_bounds__(256, 2) k_greedy(GrParams p) {
     w.bflag[n] = 0;
     w.inc[n] = 0;
   }
+  // largest column norm of A (diagonal of the Gram matrix), for the FP32 error bound of
+  // the correlation
+  double cn2 = 0.0;
+  for (int n = lane; n < N; n += 32) cn2 = fmax(cn2, p.G64[(size_t)n * N + n]);
+  const double cnorm = sqrt(warp_max(cn2));
   __syncwarp();
 
   for (;;) {
@@ -648,14 +732,17 @@ __global__ void __launch_bounds__(256, 2) k_greedy(GrParams p) {
       if (M / G < cap) cap = M / G;
     }
     bool bad = false;
+    double r2 = 0.0;
     for (int m = lane; m < M; m += 32) {
       float yv = p.Y[pix * M + m];
       bad |= !isfinite(yv);
       w.y[m] = yv;
       w.r[m] = (double)yv;  // r^0 = y
       w.rf[m] = yv;
+      r2 += (double)yv * yv;
     }
     if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(p.status, kStNonFinite);
+    double rnorm = sqrt(warp_sum(r2));  // ||r||_2, FP64
     __syncwarp();
 
     int nc = 0, nq = 0, it = 0;
@@ -687,10 +774,49 @@ __global__ void __launch_bounds__(256, 2) k_greedy(GrParams p) {
         }
       }
       const int ksel = ALGO == kGomp ? G : (ALGO == kCosamp ? 2 * kappa : kappa);
-      if (ksel > 8)
-        topk_select_atoms(w, val, N, ksel, w.sel);
-      else
-        topk_atoms(w, val, N, ksel, w.sel);
+      const float tk = ksel > 8 ? topk_select_atoms(w, val, N, ksel, w.sel)
+                                : topk_atoms(w, val, N, ksel, w.sel);
+      {
+        // FP32 error bound of the correlation: the sum of M products of rounded A and r
+        // errs by at most (M + 2) u sum |A_mj r_m| <= (M + 2) u ||A_j|| ||r||, u = 2^-24
+        const double pbound = (M + 4) * 0x1p-24 * 1.01 * cnorm * rnorm;
+        if (ALGO == kBiht) {
+          // u = x + mu p adds the roundings of x, mu and of the update itself
+          float um = 0.f, xm = 0.f;
+#pragma unroll
+          for (int kk = 0; kk < kNK; ++kk) {
+            int n = lane + 32 * kk;
+            if (n < N) {
+              um = fmaxf(um, fabsf(val[kk]));
+              xm = fmaxf(xm, fabsf(w.xd[n]));
+            }
+          }
+          um = warp_max(um);
+          xm = warp_max(xm);
+          const double E =
+              p.mu64 * pbound + 0x1p-24 * 1.01 * ((double)um + xm + p.mu64 * cnorm * rnorm);
+          certify_topk(w, val, N, ksel, tk, (float)(E * 1.001),
+                       [&](int j) {
+                         const double* a = p.At64 + (size_t)j * M;
+                         double g = 0.0;
+                         for (int m = 0; m < M; ++m) g += a[m] * w.r[m];
+                         double xj = 0.0;
+                         for (int t = 0; t < nq; ++t)
+                           if (w.q[t] == j) xj = w.xq[t];
+                         return xj + p.mu64 * g;
+                       },
+                       w.sel);
+        } else {
+          certify_topk(w, val, N, ksel, tk, (float)(pbound * 1.001),
+                       [&](int j) {
+                         const double* a = p.At64 + (size_t)j * M;
+                         double g = 0.0;
+                         for (int m = 0; m < M; ++m) g += a[m] * w.r[m];
+                         return g;
+                       },
+                       w.sel);
+        }
+      }
 
       // ---- support c (kept sorted by atom) ----
       if (ALGO == kBiht) {
@@ -784,17 +910,19 @@ __global__ void __launch_bounds__(256, 2) k_greedy(GrParams p) {
       __syncwarp();
 
       // ---- step 4: r = y - A x, Delta (FP64) ----
-      double d2 = 0.0;
+      double d2 = 0.0, rr = 0.0;
       for (int m = lane; m < M; m += 32) {
         double acc = 0.0;
         for (int j = 0; j < nq; ++j) acc += p.At64[(size_t)w.q[j] * M + m] * w.xq[j];
         double rn = (double)w.y[m] - acc;
         double df = rn - w.r[m];
         d2 += df * df;
+        rr += rn * rn;
         w.r[m] = rn;
         w.rf[m] = (float)rn;
       }
       d2 = warp_sum(d2);
+      rnorm = sqrt(warp_sum(rr));
       __syncwarp();
       work += 2.0 * M * nq;
       ++it;
@@ -851,6 +979,7 @@ cudaError_t launch_greedy(Ctx& c, GreedyAlgo algo, const GreedyArgs& a) {
   p.G = a.G;
   p.kappa_pp = a.kappa_pp;
   p.mu = (float)a.mu;
+  p.mu64 = a.mu;
   p.eps2 = a.eps * a.eps;
   p.start_done = a.eps > 1.0;
   p.max_iters = a.max_iters;
@@ -1045,6 +1174,7 @@ cudaError_t launch_gomp_noalloc(const double* A64, int M, int N, const GreedyArg
   p.G = a.G;
   p.kappa_pp = a.kappa_pp;
   p.mu = (float)a.mu;
+  p.mu64 = a.mu;
   p.eps2 = a.eps * a.eps;
   p.start_done = a.eps > 1.0;
   p.max_iters = a.max_iters;
