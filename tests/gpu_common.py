@@ -89,6 +89,17 @@ def gpu_run(call, ctx, Y, N, *args, eps=1e-8, max_iters=100, prec=0, mu=0.1, kap
     return Xd.cpu().numpy(), it.cpu().numpy(), cv.cpu().numpy()
 
 
+def exact_check(Xg, it, Xo, ito, kappa):
+    """Greedy parity on every pixel: the GPU certifies each top-k choice against FP64,
+    so supports and iteration counts equal the oracle's and the values agree to FP32
+    output rounding (cube rel-L2 <= 1e-5), near-tied or not."""
+    assert np.all((Xg != 0).sum(1) <= kappa)
+    same = np.all(support(Xg) == support(Xo), axis=1)
+    assert same.all(), f"{(~same).sum()} of {len(same)} pixels differ in support"
+    assert np.array_equal(it, ito), f"{(it != ito).sum()} pixels differ in iterations"
+    assert rel_l2(Xg, Xo) <= REL_L2_FP32
+
+
 def support_check(Xg, Xo, margins, kappa, margin_min=MARGIN_FP32):
     """Greedy parity: every output kappa-sparse; identical supports and values within the
     FP32 tolerance on well-separated pixels.  Returns the well-separated mask."""

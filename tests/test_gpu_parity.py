@@ -9,7 +9,8 @@ import pytest
 
 import oracle as orc
 from gpu_common import (MARGIN_FP32, REL_L2_FP32, Problem, fixed_iteration_tolerance,
-                        gpu_run, iterate_conditioning, library, rel_l2, support, support_check)
+                        exact_check, gpu_run, iterate_conditioning, library, rel_l2, support,
+                        support_check)
 from oracle_pins import rand_orthogonal, soft_np
 from paper_2401_14762_gb300 import synthetic as sy
 
@@ -153,16 +154,15 @@ def test_gomp_small(cs, small):
     Xo, ito, mg = orc.gomp(small.A, small.Y, 8, 2)
     ctx = cs.cs_create(small.M, small.N, Phi=small.Phi)
     Xg, it, cv = gpu_run(cs.cs_recover_gomp, ctx, small.Y, small.N, 8, 2)
-    sep = support_check(Xg, Xo, mg, 8)
-    assert np.all(it[sep] == ito[sep])
+    support_check(Xg, Xo, mg, 8)
+    exact_check(Xg, it, Xo, ito, 8)
 
 
 def test_gomp_powerlaw(cs, plaw):
     Xo, ito, mg = orc.gomp(plaw.A, plaw.Y, 20, 4)
     ctx = cs.cs_create(plaw.M, plaw.N, Phi=plaw.Phi)
     Xg, it, cv = gpu_run(cs.cs_recover_gomp, ctx, plaw.Y, plaw.N, 20, 4)
-    sep = support_check(Xg, Xo, mg, 20)
-    assert np.all(it[sep] == ito[sep])
+    exact_check(Xg, it, Xo, ito, 20)
 
 
 def test_gomp_is_omp_exact(cs):
@@ -183,16 +183,15 @@ def test_biht_small(cs, small, mu):
     Xo, ito, mg = orc.biht(small.A, small.Y, 8, mu)
     ctx = cs.cs_create(small.M, small.N, Phi=small.Phi)
     Xg, it, cv = gpu_run(cs.cs_recover_biht, ctx, small.Y, small.N, 8, mu=mu)
-    sep = support_check(Xg, Xo, mg, 8)
-    assert np.all(it[sep] == ito[sep])
+    support_check(Xg, Xo, mg, 8)
+    exact_check(Xg, it, Xo, ito, 8)
 
 
 def test_biht_powerlaw(cs, plaw):
     Xo, ito, mg = orc.biht(plaw.A, plaw.Y, 20, 0.1)
     ctx = cs.cs_create(plaw.M, plaw.N, Phi=plaw.Phi)
     Xg, it, _ = gpu_run(cs.cs_recover_biht, ctx, plaw.Y, plaw.N, 20, mu=0.1)
-    sep = support_check(Xg, Xo, mg, 20)
-    assert np.all(it[sep] == ito[sep])
+    exact_check(Xg, it, Xo, ito, 20)
 
 
 def test_biht_worked_example(cs):
@@ -207,18 +206,19 @@ def test_cosamp_small(cs, small):
     Xo, ito, mg = orc.cosamp(small.A, small.Y, 8)
     ctx = cs.cs_create(small.M, small.N, Phi=small.Phi)
     Xg, it, cv = gpu_run(cs.cs_recover_cosamp, ctx, small.Y, small.N, 8)
-    sep = support_check(Xg, Xo, mg, 8)
-    assert np.all(it[sep] == ito[sep])
+    support_check(Xg, Xo, mg, 8)
+    exact_check(Xg, it, Xo, ito, 8)
 
 
 def test_cosamp_powerlaw(cs):
-    # the 2 kappa = 40-atom cut of power-law spectra is often near-tied: take more pixels
+    # the 2 kappa = 40-atom cut of power-law spectra is often near-tied and CoSaMP
+    # oscillates up to its cap: any selection that differed from FP64 would show
     plaw = Problem(80, 200, 32 * 40 + 5, "powerlaw", seed=2, noise_var=1e-3)
     Xo, ito, mg = orc.cosamp(plaw.A, plaw.Y, 20)
     ctx = cs.cs_create(plaw.M, plaw.N, Phi=plaw.Phi)
     Xg, it, _ = gpu_run(cs.cs_recover_cosamp, ctx, plaw.Y, plaw.N, 20)
-    sep = support_check(Xg, Xo, mg, 20)
-    assert np.all(it[sep] == ito[sep])
+    assert (ito == 100).mean() > 0.3  # many pixels never converge: a long trajectory
+    exact_check(Xg, it, Xo, ito, 20)
 
 
 def test_min_norm_support(cs):
@@ -227,10 +227,7 @@ def test_min_norm_support(cs):
     Xo, ito, mg = orc.cosamp(pr.A, pr.Y, 10, max_iters=5)
     ctx = cs.cs_create(pr.M, pr.N, Phi=pr.Phi)
     Xg, it, _ = gpu_run(cs.cs_recover_cosamp, ctx, pr.Y, pr.N, 10, max_iters=5)
-    sep = mg > MARGIN_FP32
-    same = np.all(support(Xg[sep]) == support(Xo[sep]), axis=1)
-    assert same.mean() > 0.9
-    assert rel_l2(Xg[sep][same], Xo[sep][same]) < 1e-4
+    exact_check(Xg, it, Xo, ito, 10)
 
 
 def test_kappa_per_pixel(cs):
@@ -241,10 +238,12 @@ def test_kappa_per_pixel(cs):
     Xg, it, _ = gpu_run(cs.cs_recover_gomp, ctx, pr.Y, pr.N, 12, 0, kappa_pp=kp)
     Xo = np.zeros_like(pr.Xt)
     mg = np.zeros(pr.P)
+    ito = np.zeros(pr.P, dtype=it.dtype)
     for k in np.unique(kp):
         sel = kp == k
-        Xo[sel], _, mg[sel] = orc.gomp(pr.A, pr.Y[sel], int(k), max(1, int(k) // 5))
+        Xo[sel], ito[sel], mg[sel] = orc.gomp(pr.A, pr.Y[sel], int(k), max(1, int(k) // 5))
     support_check(Xg, Xo, mg, 12)
+    exact_check(Xg, it, Xo, ito, 12)
 
 
 # --------------------------------------------------------------------------- edges
