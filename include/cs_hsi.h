@@ -69,7 +69,16 @@ typedef struct {
   uint8_t *converged_out;  /* optional, device, P entries: 1 if Delta < eps was reached,
                               0 if the cap stopped it, 2 if its support LS failed */
   const int16_t *kappa_per_pixel; /* optional, device, P entries: per-pixel sparsity
-                                     for the greedy calls (overrides kappa) */
+                                     for the greedy calls; the call's kappa is then
+                                     their upper bound and values outside 0..kappa
+                                     are clamped into it */
+  /* BIHT and CoSaMP: 1 (default) lets a pixel stop iterating once its iterate x repeats
+   * an earlier one bit for bit.  Each iteration is a deterministic function of x, so the
+   * iterates are then periodic, every later Delta repeats one already tested against
+   * eps, and the cap decides: the pixel runs only the iterations that bring it to the
+   * cap's phase of the cycle.  X, iters_out and converged_out are exactly those of
+   * running every iteration.  0 runs every iteration. */
+  int cycle_skip;
 } cs_opts;
 
 /* Fills *opts with the defaults listed above. */

@@ -34,7 +34,8 @@ class CsError(RuntimeError):
 class cs_opts(ctypes.Structure):
     _fields_ = [("eps", ctypes.c_double), ("max_iters", ctypes.c_int), ("prec", ctypes.c_int),
                 ("mu", ctypes.c_double), ("iters_out", ctypes.c_void_p),
-                ("converged_out", ctypes.c_void_p), ("kappa_per_pixel", ctypes.c_void_p)]
+                ("converged_out", ctypes.c_void_p), ("kappa_per_pixel", ctypes.c_void_p),
+                ("cycle_skip", ctypes.c_int)]
 
 
 _lib = None
@@ -144,9 +145,10 @@ def cs_opts_default() -> cs_opts:
 
 
 def make_opts(eps=1e-8, max_iters=100, prec=CS_FP32, mu=0.1, iters_out=None,
-              converged_out=None, kappa_per_pixel=None) -> cs_opts:
+              converged_out=None, kappa_per_pixel=None, cycle_skip=True) -> cs_opts:
     o = cs_opts_default()
     o.eps, o.max_iters, o.prec, o.mu = float(eps), int(max_iters), int(prec), float(mu)
+    o.cycle_skip = 1 if cycle_skip else 0
     o.iters_out = _ptr(iters_out, np.int32)
     o.converged_out = _ptr(converged_out, np.uint8)
     o.kappa_per_pixel = _ptr(kappa_per_pixel, np.int16)

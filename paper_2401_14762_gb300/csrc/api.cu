@@ -41,6 +41,7 @@ void free_ctx(Ctx& c) {
   cudaFree(c.A64);
   cudaFree(c.At64);
   cudaFree(c.G64);
+  cudaFree(c.G32);
   cudaFree(c.A32);
   cudaFree(c.At32);
   cudaFree(c.W32);
@@ -125,6 +126,7 @@ void cs_opts_default(cs_opts* o) {
   o->iters_out = nullptr;
   o->converged_out = nullptr;
   o->kappa_per_pixel = nullptr;
+  o->cycle_skip = 1;
 }
 
 const char* cs_last_error(void) { return cs::g_err.c_str(); }
@@ -165,6 +167,7 @@ cs_status cs_create(cs_ctx** out, int M, int N, const double* A_host, const doub
   if ((e = cs::dalloc(&c.A64, (size_t)M * N)) != cudaSuccess ||
       (e = cs::dalloc(&c.At64, (size_t)N * M)) != cudaSuccess ||
       (e = cs::dalloc(&c.G64, (size_t)N * N)) != cudaSuccess ||
+      (e = cs::dalloc(&c.G32, (size_t)N * N)) != cudaSuccess ||
       (e = cs::dalloc(&c.A32, (size_t)M * N)) != cudaSuccess ||
       (e = cs::dalloc(&c.At32, (size_t)N * M)) != cudaSuccess ||
       (e = cs::dalloc(&c.W32, (size_t)M * M)) != cudaSuccess ||
@@ -314,7 +317,7 @@ static cs_status greedy(cs_ctx* ctx, cs::GreedyAlgo algo, const float* Y, float*
   if (P == 0) return CS_OK;
   return cs::with_cube(ctx, Y, X, P, c.M, c.N, [&](const float* Yd, float* Xd) {
     cs::GreedyArgs a{Yd, Xd, P, kappa, G, o.mu, o.eps, o.max_iters, o.kappa_per_pixel, kmax,
-                     o.iters_out, o.converged_out, o.prec};
+                     o.iters_out, o.converged_out, o.prec, o.cycle_skip != 0};
     return cs::launch_greedy(c, algo, a);
   });
 }
@@ -379,7 +382,7 @@ cs_status cs_recover_gomp_noalloc(const double* A_dev, int M, int N, const float
     return CS_ERR_NO_DEVICE;
   }
   cs::GreedyArgs a{Y, X, P, kappa, G, o.mu, o.eps, o.max_iters, o.kappa_per_pixel, kappa,
-                   o.iters_out, o.converged_out, o.prec};
+                   o.iters_out, o.converged_out, o.prec, o.cycle_skip != 0};
   e = cs::launch_gomp_noalloc(A_dev, M, N, a, static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_fail(e, "cs_recover_gomp_noalloc");
   return CS_OK;

@@ -36,6 +36,7 @@ struct Ctx {
   double* A64 = nullptr;      // M x N, FP64
   double* At64 = nullptr;     // N x M, FP64 (column j of A contiguous)
   double* G64 = nullptr;      // N x N, FP64 Gram A^T A
+  float* G32 = nullptr;       // N x N, its FP32 rounding (factor gathers)
   float* A32 = nullptr;       // M x N, FP32
   float* At32 = nullptr;      // N x M, FP32
   double rho = 0.0;           // penalty of the cached ADMM factor
@@ -100,6 +101,7 @@ struct GreedyArgs {
   int32_t* iters_out;
   uint8_t* conv_out;
   cs_precision prec;
+  bool cycle_skip;  // BIHT/CoSaMP: stop at a repeated iterate (exact, see k_greedy)
 };
 cudaError_t launch_greedy(Ctx& c, GreedyAlgo algo, const GreedyArgs& a);
 

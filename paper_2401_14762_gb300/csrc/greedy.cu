@@ -39,6 +39,7 @@ struct GrParams {
   const float* At32;   // N x M
   const double* At64;  // N x M
   const double* G64;   // N x N
+  const float* G32;    // N x N FP32 rounding of G64, or nullptr (gathers then convert)
   const float* Y;
   float* X;
   int64_t P;
@@ -58,16 +59,17 @@ struct GrParams {
   double* fb64;      // per-warp global FP64 fallback slots (nullptr: FP64 factors in smem)
   int fb_slot;       // doubles per slot
   double* work;      // optional: algorithmic flops of the call are added here
+  int cycle_skip;    // BIHT/CoSaMP: finish at the cap's phase once x repeats
 };
 
 // Byte offsets of one warp's shared-memory slice.  With fp64_smem the factor regions are
 // sized for FP64 (the fallback factorisation then runs in place); otherwise they hold
 // the FP32 factors only and the fallback uses the warp's global slot.
 struct Layout {
-  int y, rf, r, xd, b, bflag, inc, c, q, sel, tmp16, xq, L, invd, v, s, wv, Lq, invq, vq, sq,
-      svals, total;
+  int y, rf, r, xd, b, bflag, inc, c, q, sel, xq, L, invd, v, s, wv, Lq, invq, vq, sq,
+      svals, cx, cq, ring, total;
   __host__ __device__ Layout(int M, int N, int cmax, int dmax, int kmax, bool fp64_smem,
-                             bool need_q) {
+                             bool need_q, bool need_cyc) {
     const int fw = fp64_smem ? 8 : 4;
     int o = 0;
     auto take = [&](int bytes, int align) {
@@ -89,14 +91,17 @@ struct Layout {
     vq = take(8 * kq, 8);
     sq = take(8 * kq, 8);
     svals = take(8 * cmax, 8);
+    const int kc = need_cyc ? kmax : 0;  // saved iterate of the cycle search
+    cx = take(8 * kc, 8);
+    ring = take(need_cyc ? 8 * 32 : 0, 8);  // hashes of the last 32 iterates
     r = take(8 * M, 8);
     y = take(4 * M, 4);
     rf = take(4 * M, 4);
     xd = take(4 * N, 4);
     c = take(2 * cmax, 2);
     q = take(2 * kmax, 2);
+    cq = take(2 * kc, 2);
     sel = take(2 * N, 2);
-    tmp16 = take(2 * N, 2);
     bflag = take(N, 1);
     inc = take(N, 1);
     total = (o + 15) / 16 * 16;
@@ -113,7 +118,7 @@ struct Warp {
   float *y, *rf, *xd;
   double *r, *b, *xq, *L, *invd, *v, *s, *wv, *Lq, *invq, *vq, *sq, *svals;
   uint8_t *bflag, *inc;
-  int16_t *c, *q, *sel, *tmp16;
+  int16_t *c, *q, *sel;
   double* fb;  // this warp's global FP64 fallback slot, or nullptr
 };
 
@@ -239,59 +244,117 @@ __device__ void fill_rhs(Warp& w, const int16_t* atoms, int n, double* out) {
   __syncwarp();
 }
 
-// Gathers G_c (FP32) into the packed column-major lower triangle L and factors it in
-// place, right-looking.  Lane l owns rows l, l+32, ...; at step j the column values
-// L(k, j) reach every lane by shuffle, so the trailing update L(i, k) -= L(i, j) L(k, j)
-// runs in lock step over k with conflict-free shared-memory traffic.  Returns false when
-// a pivot drops below 1e-4 of its original diagonal (FP32 would lose the factor).
+// FP32 factors are packed row-major lower triangles: entry (i, k), k <= i, at
+// i(i+1)/2 + k.  The triangular numbers i(i+1)/2 for 32 consecutive i are distinct
+// mod 32, so 32 lanes reading one column of 32 consecutive rows hit 32 different banks,
+// as do lanes reading along a row.
+__device__ __forceinline__ int ridx(int i, int k) { return (i * (i + 1) >> 1) + k; }
+
+// Gathers G_c (FP32) into L and factors it in place, left-looking in blocks of CB
+// columns (four for systems of up to 64 rows, one beyond): lane l owns rows l, l+32, ...;
+// for the block's columns j..j+CB-1 every owned row i accumulates
+// t_i,c = G(i, j+c) - sum_{k<j} L(i, k) L(j+c, k) (one load of L(i, k) feeds CB
+// products; rows j..j+CB-1 are read by broadcast), then the block's columns
+// are finished in order: t_i,c -= L(i, j+c') L(j+c, j+c') for the block's earlier
+// columns c' (shuffled from the owners of rows j+c), L(j+c, j+c) = sqrt(t_{j+c},c) and
+// L(i, j+c) = t_i,c / L(j+c, j+c).  Returns false when a pivot drops below 1e-4 of its
+// original diagonal (FP32 would lose the factor).  invd ends up holding 1 / L(j, j).
 template <int VR>
-__device__ bool chol32(Warp& w, float* L, float* invd, int cap, int n, const int16_t* atoms) {
+__device__ bool chol32(Warp& w, float* L, float* invd, int n, const int16_t* atoms) {
   const int lane = w.lane, N = w.p.N;
-  const double* G = w.p.G64;
-  for (int k = 0; k < n; ++k) {
-    const double* grow = G + (size_t)atoms[k] * N;
-    const int ck = lidx(0, k, cap);
-    for (int i = k + lane; i < n; i += 32) {
-      float g = (float)grow[atoms[i]];
-      L[ck + i] = g;
-      if (i == k) invd[k] = g;  // original diagonal, for the pivot test
+  // gather: G row atoms[k] (read at the sorted atoms, a few sectors) into column k;
+  // several columns of loads are in flight before their stores
+  constexpr int kB = VR <= 2 ? 8 : 4;
+  const float* G32 = w.p.G32;
+  const double* G64 = w.p.G64;
+  for (int k0 = 0; k0 < n; k0 += kB) {
+    float g[kB][VR];
+#pragma unroll
+    for (int kk = 0; kk < kB; ++kk) {
+      const int k = k0 + kk;
+      const size_t row = (size_t)atoms[min(k, n - 1)] * N;
+#pragma unroll
+      for (int r = 0; r < VR; ++r) {
+        const int i = k + lane + 32 * r;
+        const int col = atoms[min(i, n - 1)];  // clamped lanes are not stored
+        g[kk][r] = 0.f;
+        if (k + 32 * r < n) g[kk][r] = G32 ? __ldg(G32 + row + col) : (float)__ldg(G64 + row + col);
+      }
+    }
+#pragma unroll
+    for (int kk = 0; kk < kB; ++kk) {
+      const int k = k0 + kk;
+#pragma unroll
+      for (int r = 0; r < VR; ++r) {
+        const int i = k + lane + 32 * r;
+        if (k < n && i < n) {
+          L[ridx(i, k)] = g[kk][r];
+          if (i == k) invd[k] = g[kk][r];  // original diagonal, for the pivot test
+        }
+      }
     }
   }
   __syncwarp();
-  for (int j = 0; j < n; ++j) {
-    const int cj = lidx(0, j, cap);
-    float d = L[cj + j];
-    if (!(d > 1e-4f * invd[j])) return false;  // warp-uniform
-    float dj = sqrtf(d), inv = 1.f / dj;
-    float lij[VR];
+  int base[VR];  // start of each owned row (clamped in range for lanes past n)
 #pragma unroll
-    for (int r = 0; r < VR; ++r) {
-      int i = lane + 32 * r;
-      lij[r] = 0.f;
-      if (i > j && i < n) {
-        lij[r] = L[cj + i] * inv;
-        L[cj + i] = lij[r];
+  for (int r = 0; r < VR; ++r) base[r] = ridx(min(lane + 32 * r, n - 1), 0);
+  constexpr int CB = VR <= 2 ? 4 : 1;  // columns per block (measured: wider systems lose)
+  for (int j = 0; j < n; j += CB) {
+    const int nb = min(CB, n - j);  // columns in this block
+    const float* R[CB];             // rows j..j+CB-1 (clamped past n: read, unused)
+#pragma unroll
+    for (int c = 0; c < CB; ++c) R[c] = L + ridx(min(j + c, n - 1), 0);
+    float t[VR][CB];
+#pragma unroll
+    for (int r = 0; r < VR; ++r)
+#pragma unroll
+      for (int c = 0; c < CB; ++c)
+        t[r][c] = c < nb ? L[base[r] + j + c] : 0.f;  // G(i, j+c); rows above are discarded
+    // rows that end before k read into the next row, inside the triangle (discarded)
+    for (int k = 0; k < j; ++k) {
+      float b[CB];
+#pragma unroll
+      for (int c = 0; c < CB; ++c) b[c] = R[c][k];
+#pragma unroll
+      for (int r = 0; r < VR; ++r) {
+        if (32 * r + 31 >= j && 32 * r < n) {  // warp-uniform: the slot owns rows >= j
+          const float l = L[base[r] + k];
+#pragma unroll
+          for (int c = 0; c < CB; ++c) t[r][c] = fmaf(-l, b[c], t[r][c]);
+        }
       }
     }
-    if (lane == 0) {
-      L[cj + j] = dj;
-      invd[j] = inv;
-    }
-    // k in slot r's range [32r, 32r + 32): only lanes of slots >= r own rows i >= k, and
-    // L(k, j) comes from lane k - 32r's slot-r value
-    int ck = lidx(0, j + 1, cap);
+    float lc[VR][CB];  // the block's finished columns, L(i, j+c), per owned row
 #pragma unroll
-    for (int rs = 0; rs < VR; ++rs) {
-      const int kbeg = max(j + 1, 32 * rs), kend = min(n, 32 * rs + 32);
-#pragma unroll 2
-      for (int k = kbeg; k < kend; ++k) {
-        const float lkj = __shfl_sync(0xffffffffu, lij[rs], k - 32 * rs);
+    for (int c = 0; c < CB; ++c) {
+      if (c < nb) {  // warp-uniform
+        const int col = j + c, src = col & 31, slot = col >> 5;
 #pragma unroll
-        for (int r = rs; r < VR; ++r) {
-          const int i = lane + 32 * r;
-          if (i >= k && i < n) L[ck + i] = fmaf(-lij[r], lkj, L[ck + i]);
+        for (int c2 = 0; c2 < c; ++c2) {
+          // L(j+c, j+c2) from the owner of row j+c
+          float own[VR];
+#pragma unroll
+          for (int r = 0; r < VR; ++r) own[r] = lc[r][c2];
+          const float lcc = __shfl_sync(0xffffffffu, rpick<VR>(own, slot), src);
+#pragma unroll
+          for (int r = 0; r < VR; ++r) t[r][c] = fmaf(-lc[r][c2], lcc, t[r][c]);
         }
-        ck += cap - k - 1;
+        float tc[VR];
+#pragma unroll
+        for (int r = 0; r < VR; ++r) tc[r] = t[r][c];
+        const float d = __shfl_sync(0xffffffffu, rpick<VR>(tc, slot), src);
+        if (!(d > 1e-4f * invd[col])) return false;  // warp-uniform
+        const float dj = sqrtf(d), inv = 1.f / dj;
+#pragma unroll
+        for (int r = 0; r < VR; ++r) {
+          const int i = lane + 32 * r;
+          lc[r][c] = i > col ? t[r][c] * inv : 0.f;
+          if (i > col && i < n) L[base[r] + col] = lc[r][c];
+        }
+        if (lane == 0) {
+          L[ridx(col, col)] = dj;
+          invd[col] = inv;
+        }
       }
     }
     __syncwarp();
@@ -299,29 +362,30 @@ __device__ bool chol32(Warp& w, float* L, float* invd, int cap, int n, const int
   return true;
 }
 
-// v := L^{-1} v and v := L^{-T} v on register-distributed vectors.
+// v := L^{-1} v (column sweeps: lanes t > i read L(t, i)) and v := L^{-T} v (row sweeps:
+// lanes t < i read L(i, t)) on register-distributed vectors.
 template <int VR>
-__device__ void fwd32(const float* L, const float* invd, int cap, int n, float (&v)[VR], int lane) {
+__device__ void fwd32(const float* L, const float* invd, int n, float (&v)[VR], int lane) {
   for (int i = 0; i < n; ++i) {
     float vi = __shfl_sync(0xffffffffu, rpick<VR>(v, i >> 5), i & 31) * invd[i];
-    const float* col = L + lidx(0, i, cap);
 #pragma unroll
     for (int k = 0; k < VR; ++k) {
       int t = lane + 32 * k;
       if (t == i) v[k] = vi;
-      else if (t > i && t < n) v[k] = fmaf(-col[t], vi, v[k]);
+      else if (t > i && t < n) v[k] = fmaf(-L[ridx(t, i)], vi, v[k]);
     }
   }
 }
 template <int VR>
-__device__ void bwd32(const float* L, const float* invd, int cap, int n, float (&v)[VR], int lane) {
+__device__ void bwd32(const float* L, const float* invd, int n, float (&v)[VR], int lane) {
   for (int i = n - 1; i >= 0; --i) {
     float si = __shfl_sync(0xffffffffu, rpick<VR>(v, i >> 5), i & 31) * invd[i];
+    const float* row = L + ridx(i, 0);
 #pragma unroll
     for (int k = 0; k < VR; ++k) {
       int t = lane + 32 * k;
       if (t == i) v[k] = si;
-      else if (t < i) v[k] = fmaf(-L[lidx(i, t, cap)], si, v[k]);
+      else if (t < i) v[k] = fmaf(-row[t], si, v[k]);
     }
   }
 }
@@ -330,7 +394,7 @@ __device__ void bwd32(const float* L, const float* invd, int cap, int n, float (
 // 1e-9 of the solution (the solution then carries FP64-level accuracy), false if the
 // corrections stop contracting (the system is too ill-conditioned for an FP32 factor).
 template <int VR>
-__device__ bool refine32(Warp& w, const float* L, const float* invd, int cap, int n,
+__device__ bool refine32(Warp& w, const float* L, const float* invd, int n,
                          const int16_t* atoms, const double* b, double* s) {
   const int lane = w.lane, N = w.p.N;
   const double* G = w.p.G64;
@@ -346,8 +410,8 @@ __device__ bool refine32(Warp& w, const float* L, const float* invd, int cap, in
     float f[VR];
 #pragma unroll
     for (int k = 0; k < VR; ++k) f[k] = (float)rr[k];
-    fwd32<VR>(L, invd, cap, n, f, lane);
-    bwd32<VR>(L, invd, cap, n, f, lane);
+    fwd32<VR>(L, invd, n, f, lane);
+    bwd32<VR>(L, invd, n, f, lane);
     float dm = 0.f;
     double sm = 0.0;
 #pragma unroll
@@ -366,23 +430,36 @@ __device__ bool refine32(Warp& w, const float* L, const float* invd, int cap, in
     if ((double)dm <= 1e-9 * sm) return true;
     if (step > 0 && dm > 0.5f * prev) return false;
     prev = dm;
-    // r = b - G_c s in FP64
+    // r = b - G_c s in FP64; by symmetry lane t reads G(c_j, c_t) from row c_j, so a
+    // warp's loads fall in one row at the sorted atoms; eight rows of loads in flight
+    {
+      int col[VR];
+      double acc[VR][2];
 #pragma unroll
-    for (int k = 0; k < VR; ++k) {
-      int t = lane + 32 * k;
-      if (t < n) {
-        const double* grow = G + (size_t)atoms[t] * N;
-        double a0 = b[t], a1 = 0.0, a2 = 0.0, a3 = 0.0;
-        int j = 0;
-        for (; j + 3 < n; j += 4) {
-          a0 -= grow[atoms[j]] * s[j];
-          a1 -= grow[atoms[j + 1]] * s[j + 1];
-          a2 -= grow[atoms[j + 2]] * s[j + 2];
-          a3 -= grow[atoms[j + 3]] * s[j + 3];
-        }
-        for (; j < n; ++j) a0 -= grow[atoms[j]] * s[j];
-        rr[k] = (a0 + a1) + (a2 + a3);
+      for (int k = 0; k < VR; ++k) {
+        const int t = lane + 32 * k;
+        col[k] = atoms[min(t, n - 1)];
+        acc[k][0] = t < n ? b[t] : 0.0;
+        acc[k][1] = 0.0;
       }
+      constexpr int kB = VR <= 2 ? 8 : 4;
+      for (int j0 = 0; j0 < n; j0 += kB) {
+        double g[kB][VR];
+#pragma unroll
+        for (int jj = 0; jj < kB; ++jj) {
+          const double* grow = G + (size_t)atoms[min(j0 + jj, n - 1)] * N;
+#pragma unroll
+          for (int k = 0; k < VR; ++k) g[jj][k] = 32 * k < n ? __ldg(grow + col[k]) : 0.0;
+        }
+#pragma unroll
+        for (int jj = 0; jj < kB; ++jj) {
+          const double sj = j0 + jj < n ? s[j0 + jj] : 0.0;
+#pragma unroll
+          for (int k = 0; k < VR; ++k) acc[k][jj & 1] = fma(-g[jj][k], sj, acc[k][jj & 1]);
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < VR; ++k) rr[k] = lane + 32 * k < n ? acc[k][0] + acc[k][1] : 0.0;
     }
   }
   return false;
@@ -583,25 +660,6 @@ __device__ void certify_topk(Warp& w, const float (&val)[kNK], int nvalid, int k
   __syncwarp();
 }
 
-// Sorts atoms[0..n) ascending by rank (equal keys keep their order, so every rank is
-// written even if a key repeats), carrying FP64 values if given.
-__device__ void sort_atoms(Warp& w, int16_t* atoms, double* vals, int n) {
-  int16_t* tmp = w.tmp16;
-  double* tv = w.wv;
-  for (int j = w.lane; j < n; j += 32) {
-    int a = atoms[j], rank = 0;
-    for (int t = 0; t < n; ++t) rank += atoms[t] < a || (atoms[t] == a && t < j);
-    tmp[rank] = (int16_t)a;
-    if (vals) tv[rank] = vals[j];
-  }
-  __syncwarp();
-  for (int j = w.lane; j < n; j += 32) {
-    atoms[j] = tmp[j];
-    if (vals) vals[j] = tv[j];
-  }
-  __syncwarp();
-}
-
 // Fresh factorisation of the normal equations on atoms[0..n) and solve into s.
 __device__ bool ls_fresh(Warp& w, const int16_t* atoms, int n, double* L, double* invd, double* v,
                          double* s, int cap) {
@@ -624,7 +682,7 @@ __device__ bool ls_solve(Warp& w, const int16_t* atoms, int n, double* Lbuf, dou
   fill_rhs(w, atoms, n, vbuf);
   float* L32 = reinterpret_cast<float*>(Lbuf);
   float* inv32 = reinterpret_cast<float*>(invdbuf);
-  if (chol32<VR>(w, L32, inv32, cap, n, atoms) && refine32<VR>(w, L32, inv32, cap, n, atoms, vbuf, s))
+  if (chol32<VR>(w, L32, inv32, n, atoms) && refine32<VR>(w, L32, inv32, n, atoms, vbuf, s))
     return true;
   // FP64 fallback: in place when the shared regions are FP64-sized, else in the warp's
   // global slot (capacity dmax >= n)
@@ -673,12 +731,32 @@ __device__ bool ls_min_norm(Warp& w, const int16_t* atoms, int n, double* s) {
   return true;
 }
 
+// SplitMix64's output mixing function (Steele, Lea and Flood, OOPSLA 2014).
+__device__ __forceinline__ unsigned long long mix64(unsigned long long z) {
+  z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+  z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+  return z ^ (z >> 31);
+}
+
+// 64-bit hash of the iterate x (its nq kept atoms w.q and values w.xq, bit patterns and
+// positions), the same on every lane.  A match only nominates a cycle; the cycle search
+// confirms it bit for bit.
+__device__ unsigned long long iterate_hash(Warp& w, int nq) {
+  unsigned long long h = 0;
+  for (int j = w.lane; j < nq; j += 32)
+    h ^= mix64(mix64((unsigned long long)__double_as_longlong(w.xq[j])) ^
+               ((unsigned long long)(uint16_t)w.q[j] | ((unsigned long long)j << 16)));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) h ^= __shfl_xor_sync(0xffffffffu, h, o);
+  return h ^ mix64(0x5eedull + (unsigned long long)nq);
+}
+
 template <int ALGO, int VR>
 __global__ void __launch_bounds__(256, 2) k_greedy(GrParams p) {
   extern __shared__ __align__(16) unsigned char gsm[];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int M = p.M, N = p.N;
-  Layout lay(M, N, p.cmax, p.dmax, p.kmax, p.fb64 == nullptr, ALGO == kGomp);
+  Layout lay(M, N, p.cmax, p.dmax, p.kmax, p.fb64 == nullptr, ALGO == kGomp, ALGO != kGomp);
   unsigned char* base = gsm + (size_t)wid * p.warp_bytes;
   Warp w{p, lane};
   w.y = (float*)(base + lay.y);
@@ -697,12 +775,14 @@ __global__ void __launch_bounds__(256, 2) k_greedy(GrParams p) {
   w.vq = (double*)(base + lay.vq);
   w.sq = (double*)(base + lay.sq);
   w.svals = (double*)(base + lay.svals);
+  double* const cyc_x = (double*)(base + lay.cx);
+  int16_t* const cyc_q = (int16_t*)(base + lay.cq);
+  unsigned long long* const ring = (unsigned long long*)(base + lay.ring);
   w.bflag = base + lay.bflag;
   w.inc = base + lay.inc;
   w.c = (int16_t*)(base + lay.c);
   w.q = (int16_t*)(base + lay.q);
   w.sel = (int16_t*)(base + lay.sel);
-  w.tmp16 = (int16_t*)(base + lay.tmp16);
   w.fb = p.fb64 ? p.fb64 + (size_t)(blockIdx.x * (blockDim.x >> 5) + wid) * p.fb_slot : nullptr;
 
   for (int n = lane; n < N; n += 32) {
@@ -724,7 +804,8 @@ __global__ void __launch_bounds__(256, 2) k_greedy(GrParams p) {
     if (pix_u >= (unsigned long long)p.P) break;
     const int64_t pix = (int64_t)pix_u;
 
-    const int kappa = p.kappa_pp ? (int)p.kappa_pp[pix] : p.kappa;
+    // a per-pixel level outside 0..kappa bound is clamped: the workspace holds kmax atoms
+    const int kappa = p.kappa_pp ? min(max((int)p.kappa_pp[pix], 0), p.kmax) : p.kappa;
     const int G = p.G > 0 ? p.G : (kappa / 5 > 1 ? kappa / 5 : 1);
     int cap = p.max_iters;
     if (ALGO == kGomp) {
@@ -747,6 +828,16 @@ __global__ void __launch_bounds__(256, 2) k_greedy(GrParams p) {
 
     int nc = 0, nq = 0, it = 0;
     uint8_t conv = 0;
+    // cycle search over the iterates x_it (BIHT, CoSaMP): ring[it % 32] holds a hash of
+    // x_it; a hash seen `period` iterations ago nominates a cycle, which is confirmed by
+    // comparing x bit for bit one period later (verify_at); `full` is the cap reported
+    int saved_n = 0, full = 0, period = 0, verify_at = -1;
+    bool cycled = false;
+    if (ALGO != kGomp) {
+      const unsigned long long h0 = iterate_hash(w, 0);  // x_0 = 0 (all lanes shuffle)
+      if (lane == 0) ring[0] = h0;
+      __syncwarp();
+    }
     // algorithmic flops of the method for this pixel: correlation 2MN, Cholesky least
     // squares n^3/3 + 2n^2 per support of n atoms (min-norm form for n > M), residual 2M|q|
     double work = 0.0;
@@ -818,43 +909,29 @@ __global__ void __launch_bounds__(256, 2) k_greedy(GrParams p) {
         }
       }
 
-      // ---- support c (kept sorted by atom) ----
+      // ---- support c = Theta U c (gOMP: the growing support; CoSaMP: the last pruned
+      // support; BIHT: supp(x)), marked in inc[] and listed in ascending atom order ----
       if (ALGO == kBiht) {
-        // c = supp(x): the nonzero entries of the previous x, compacted by ballot
-        const unsigned below = (1u << lane) - 1u;
         for (int n = lane; n < N; n += 32) w.inc[n] = 0;
         __syncwarp();
+        for (int j = lane; j < nq; j += 32)
+          if (w.xq[j] != 0.0) w.inc[w.q[j]] = 1;
+      }
+      for (int j = lane; j < ksel; j += 32) w.inc[w.sel[j]] = 1;
+      __syncwarp();
+      {
+        const unsigned below = (1u << lane) - 1u;
         int cnt = 0;
-        for (int base = 0; base < nq; base += 32) {
-          int j = base + lane;
-          bool nz = j < nq && w.xq[j] != 0.0;
-          unsigned m = __ballot_sync(0xffffffffu, nz);
-          if (nz) {
-            w.c[cnt + __popc(m & below)] = w.q[j];
-            w.inc[w.q[j]] = 1;
-          }
+        for (int a0 = 0; a0 < N; a0 += 32) {
+          const int a = a0 + lane;
+          const bool in = a < N && w.inc[a];
+          const unsigned m = __ballot_sync(0xffffffffu, in);
+          if (in) w.c[cnt + __popc(m & below)] = (int16_t)a;
           cnt += __popc(m);
         }
         nc = cnt;
         __syncwarp();
       }
-      // c = Theta U c (gOMP: the growing support; CoSaMP: the last pruned support)
-      {
-        const unsigned below = (1u << lane) - 1u;
-        for (int base = 0; base < ksel; base += 32) {
-          int j = base + lane;
-          int a = j < ksel ? w.sel[j] : 0;
-          bool isnew = j < ksel && !w.inc[a];
-          unsigned m = __ballot_sync(0xffffffffu, isnew);
-          if (isnew) {
-            w.c[nc + __popc(m & below)] = (int16_t)a;
-            w.inc[a] = 1;
-          }
-          nc += __popc(m);
-          __syncwarp();
-        }
-      }
-      sort_atoms(w, w.c, nullptr, nc);
 
       // ---- step 2: least squares on c ----
       if (nc > 0) {
@@ -911,15 +988,30 @@ __global__ void __launch_bounds__(256, 2) k_greedy(GrParams p) {
 
       // ---- step 4: r = y - A x, Delta (FP64) ----
       double d2 = 0.0, rr = 0.0;
-      for (int m = lane; m < M; m += 32) {
-        double acc = 0.0;
-        for (int j = 0; j < nq; ++j) acc += p.At64[(size_t)w.q[j] * M + m] * w.xq[j];
-        double rn = (double)w.y[m] - acc;
-        double df = rn - w.r[m];
-        d2 += df * df;
-        rr += rn * rn;
-        w.r[m] = rn;
-        w.rf[m] = (float)rn;
+      {
+        // lanes own rows m = lane + 32 kk (M <= 128); atom columns of A^T are contiguous
+        double acc[4] = {0.0, 0.0, 0.0, 0.0};
+        const int mc = M - 1;
+#pragma unroll 4
+        for (int j = 0; j < nq; ++j) {
+          const double* col = p.At64 + (size_t)w.q[j] * M;
+          const double xj = w.xq[j];
+#pragma unroll
+          for (int kk = 0; kk < 4; ++kk)
+            if (32 * kk < M) acc[kk] = fma(__ldg(col + min(lane + 32 * kk, mc)), xj, acc[kk]);
+        }
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk) {
+          const int m = lane + 32 * kk;
+          if (m < M) {
+            double rn = (double)w.y[m] - acc[kk];
+            double df = rn - w.r[m];
+            d2 += df * df;
+            rr += rn * rn;
+            w.r[m] = rn;
+            w.rf[m] = (float)rn;
+          }
+        }
       }
       d2 = warp_sum(d2);
       rnorm = sqrt(warp_sum(rr));
@@ -930,7 +1022,49 @@ __global__ void __launch_bounds__(256, 2) k_greedy(GrParams p) {
         conv = 1;
         break;
       }
+      if (ALGO != kGomp && p.cycle_skip && !cycled) {
+        // x_it determines everything the next iteration computes (r, the correlation,
+        // c, the least squares and the prune run deterministically on it), so once
+        // x_{i+period} equals x_i bit for bit the iterates repeat with that period.
+        // Every later Delta then repeats one already tested against eps, so only the
+        // cap can stop the pixel: run just the iterations that reach the cap's phase of
+        // the cycle and report the cap.
+        const unsigned long long h = iterate_hash(w, nq);
+        if (it == verify_at) {
+          bool same = nq == saved_n;
+          if (same) {
+            bool eq = true;
+            for (int j = lane; j < nq; j += 32)
+              eq &= cyc_q[j] == w.q[j] &&
+                    __double_as_longlong(cyc_x[j]) == __double_as_longlong(w.xq[j]);
+            same = __all_sync(0xffffffffu, eq);
+          }
+          if (same) {
+            full = cap;
+            cap = it + (cap - it) % period;
+            cycled = true;
+          }
+          verify_at = -1;
+        } else if (verify_at < 0) {
+          // lane l tests the iterate l + 1 iterations back
+          const bool hit = lane + 1 <= it && ring[(it - lane - 1) & 31] == h;
+          const unsigned m = __ballot_sync(0xffffffffu, hit);
+          if (m) {
+            period = __ffs(m);
+            for (int j = lane; j < nq; j += 32) {
+              cyc_q[j] = w.q[j];
+              cyc_x[j] = w.xq[j];
+            }
+            saved_n = nq;
+            verify_at = it + period;
+          }
+        }
+        __syncwarp();
+        if (lane == 0) ring[it & 31] = h;
+        __syncwarp();
+      }
     }
+    if (cycled && !fail && conv == 0) it = full;
     if (fail) {
       conv = 2;
       if (lane == 0) atomicOr(p.status, kStNotSpd);
@@ -972,6 +1106,7 @@ cudaError_t launch_greedy(Ctx& c, GreedyAlgo algo, const GreedyArgs& a) {
   p.At32 = c.At32;
   p.At64 = c.At64;
   p.G64 = c.G64;
+  p.G32 = c.G32;
   p.Y = a.Y;
   p.X = a.X;
   p.P = a.P;
@@ -988,6 +1123,7 @@ cudaError_t launch_greedy(Ctx& c, GreedyAlgo algo, const GreedyArgs& a) {
   p.status = c.status;
   p.counter = reinterpret_cast<unsigned long long*>(c.counter);
   p.work = c.work;
+  p.cycle_skip = a.cycle_skip ? 1 : 0;
   const int K = a.kappa_max;
   const int M = c.M, N = c.N;
   int cmax;
@@ -1008,7 +1144,7 @@ cudaError_t launch_greedy(Ctx& c, GreedyAlgo algo, const GreedyArgs& a) {
   p.kmax = K > 0 ? K : 1;
   // FP32 factors in shared memory; the rare FP64 fallback (and the |c| > M minimum-norm
   // solve) use one global slot per resident warp, so more warps fit on an SM.
-  Layout lay(M, N, p.cmax, p.dmax, p.kmax, false, algo == kGomp);
+  Layout lay(M, N, p.cmax, p.dmax, p.kmax, false, algo == kGomp, algo != kGomp);
   p.warp_bytes = lay.total;
   // one CTA of up to 8 warps per SM, or two smaller ones if that seats more warps
   int warps1 = (220 * 1024) / lay.total, warps2 = (110 * 1024) / lay.total;
@@ -1192,7 +1328,7 @@ cudaError_t launch_gomp_noalloc(const double* A64, int M, int N, const GreedyArg
   p.cmax = cmax;
   p.dmax = cmax < M ? cmax : M;
   p.kmax = K > 0 ? K : 1;
-  Layout wl(M, N, p.cmax, p.dmax, p.kmax, true, true);
+  Layout wl(M, N, p.cmax, p.dmax, p.kmax, true, true, false);
   p.warp_bytes = wl.total;
   int warps = (220 * 1024) / wl.total;
   if (warps > 8) warps = 8;

@@ -234,6 +234,7 @@ cudaError_t setup_dictionary(Ctx& c, const double* A_host, const double* Phi_hos
   k_gemm_f64<<<nblk(M * M, 256), 256, 0, s>>>(M, M, N, c.A64, N, 1, c.A64, 1, N, S);
   k_cast_f32<<<nblk(M * N, 256), 256, 0, s>>>(M * N, c.A64, c.A32);
   k_cast_f32<<<nblk(M * N, 256), 256, 0, s>>>(M * N, c.At64, c.At32);
+  k_cast_f32<<<nblk(N * N, 256), 256, 0, s>>>(N * N, c.G64, c.G32);
   k_lambda_max<<<1, 1024, 0, s>>>(M, S, B0, B1, v, lam);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;

@@ -72,7 +72,8 @@ def rel_l2(X, ref):
     return float(np.linalg.norm(np.asarray(X, np.float64) - ref) / (d if d > 0 else 1.0))
 
 
-def gpu_run(call, ctx, Y, N, *args, eps=1e-8, max_iters=100, prec=0, mu=0.1, kappa_pp=None):
+def gpu_run(call, ctx, Y, N, *args, eps=1e-8, max_iters=100, prec=0, mu=0.1, kappa_pp=None,
+            cycle_skip=True):
     """Runs one recovery call on device copies of Y; returns (X, iters, converged) on host."""
     torch = torch_cuda()
     from paper_2401_14762_gb300 import cs
@@ -83,7 +84,7 @@ def gpu_run(call, ctx, Y, N, *args, eps=1e-8, max_iters=100, prec=0, mu=0.1, kap
     cv = torch.full((P,), 255, device="cuda", dtype=torch.uint8)
     kp = None if kappa_pp is None else torch.from_numpy(kappa_pp.astype(np.int16)).cuda()
     opts = cs.make_opts(eps=eps, max_iters=max_iters, prec=prec, mu=mu, iters_out=it,
-                        converged_out=cv, kappa_per_pixel=kp)
+                        converged_out=cv, kappa_per_pixel=kp, cycle_skip=cycle_skip)
     call(ctx, Yd, Xd, *args, opts=opts)
     cs.cs_sync(ctx)
     return Xd.cpu().numpy(), it.cpu().numpy(), cv.cpu().numpy()

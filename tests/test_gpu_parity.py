@@ -221,6 +221,24 @@ def test_cosamp_powerlaw(cs):
     exact_check(Xg, it, Xo, ito, 20)
 
 
+@pytest.mark.parametrize("algo", ["biht", "cosamp"])
+def test_cycle_skip_is_exact(cs, algo):
+    """Stopping at a repeated iterate changes nothing: X, iteration counts and flags are
+    bit for bit those of running every iteration, with less work done."""
+    pr = Problem(80, 200, 32 * 12 + 7, "powerlaw", seed=5, noise_var=1e-3)
+    ctx = cs.cs_create(pr.M, pr.N, Phi=pr.Phi)
+    call = cs.cs_recover_biht if algo == "biht" else cs.cs_recover_cosamp
+    runs = []
+    for skip in (True, False):
+        runs.append(gpu_run(call, ctx, pr.Y, pr.N, 20, mu=1.0 if algo == "biht" else 0.1,
+                            cycle_skip=skip, eps=0.0 if algo == "biht" else 1e-8))
+        runs[-1] += (cs.cs_get_work(ctx),)
+    (Xs, its, cvs, ws), (Xf, itf, cvf, wf) = runs
+    assert np.array_equal(Xs.view(np.uint32), Xf.view(np.uint32))
+    assert np.array_equal(its, itf) and np.array_equal(cvs, cvf)
+    assert (itf == 100).mean() > 0.3 and ws < 0.8 * wf
+
+
 def test_min_norm_support(cs):
     """CoSaMP with 3 kappa > M: supports larger than M take the minimum-norm solution."""
     pr = Problem(24, 60, 70, "sparse", seed=12, S=10)

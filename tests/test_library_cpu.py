@@ -36,6 +36,7 @@ def test_defaults(lib):
     o = cs.cs_opts_default()
     assert o.eps == 1e-8 and o.max_iters == 100 and o.prec == cs.CS_FP32 and o.mu == 0.1
     assert o.iters_out is None and o.converged_out is None and o.kappa_per_pixel is None
+    assert o.cycle_skip == 1
 
 
 def test_errors_before_any_device_work(lib):
