@@ -123,7 +123,12 @@ cs_status cs_recover_fista(cs_ctx *ctx, const float *Y, float *X, int64_t P, dou
  * point is the Eq. 2 LASSO solution): x^0 = z^0 = w^0 = 0; per iteration
  *   x = (A^T A + rho I)^{-1}(A^T y + rho (z - w)), z = soft(x + w, lambda/rho),
  *   w = w + x - z, Delta = ||A x - A x_prev||;
- * until Delta < opts->eps or `iters` iterations.  rho > 0, lambda >= 0.  Returns x. */
+ * until Delta < opts->eps or `iters` iterations.  rho > 0, lambda >= 0.  Returns x.
+ * The x-update runs as h = W (y - A d), x = d + A^T h with d = z - w and
+ * W = (A A^T + rho I)^{-1} factored once in FP64.  prec = CS_BF16 runs its three
+ * products on the tensor cores with split-BF16 operands (about 16 bits each, FP32
+ * accumulation) where the 128-pixel tile fits in shared memory (for example N = 200,
+ * M = 80); other shapes use the FP32 path. */
 cs_status cs_recover_admm(cs_ctx *ctx, const float *Y, float *X, int64_t P, double rho,
                           double lambda, int iters, const cs_opts *opts);
 

@@ -541,6 +541,7 @@ cudaError_t launch_fista(Ctx& c, const ConvexArgs& a) {
 }
 
 cudaError_t launch_admm(const Ctx& c, const ConvexArgs& a) {
+  if (a.P > 0 && a.prec != CS_FP32 && admm_tc_supported(c.M, c.N)) return launch_admm_tc(c, a);
   CvParams p = base_params(c);
   p.Y = a.Y;
   p.X = a.X;

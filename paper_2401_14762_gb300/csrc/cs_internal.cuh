@@ -41,6 +41,7 @@ struct Ctx {
   float* At32 = nullptr;      // N x M, FP32
   double rho = 0.0;           // penalty of the cached ADMM factor
   float* W32 = nullptr;       // M x M, FP32 (A A^T + rho I)^{-1}
+  double* W64 = nullptr;      // M x M, the same in FP64 (split for the tensor cores)
   double* scratch64 = nullptr;  // setup scratch
   size_t scratch_elems = 0;
   int* status = nullptr;      // device status word
@@ -84,6 +85,8 @@ cudaError_t launch_fista(Ctx& c, const ConvexArgs& a);
 bool fista_tc_supported(int M, int N);
 cudaError_t launch_fista_tc(const Ctx& c, const ConvexArgs& a);
 cudaError_t launch_admm(const Ctx& c, const ConvexArgs& a);
+bool admm_tc_supported(int M, int N);
+cudaError_t launch_admm_tc(const Ctx& c, const ConvexArgs& a);
 
 // ---- greedy (gOMP / BIHT / CoSaMP) ----
 enum GreedyAlgo { kGomp = 0, kBiht = 1, kCosamp = 2 };

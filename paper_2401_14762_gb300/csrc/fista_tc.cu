@@ -38,28 +38,8 @@ struct FtcParams {
   const float* beta;  // momentum weights beta_i, i = 1..iters
 };
 
-__device__ __forceinline__ float soft_thr(float a, float t) {
-  float m = fabsf(a) - t;
-  return m > 0.f ? copysignf(m, a) : 0.f;
-}
-
-// A (M x N) in the dual layout: element (m, n) at (m/8) S + (n/8) 128 + (m%8) 16 + (n%8) 2,
-// S = 16 Np.  Read K-major along n (rows m, SBO = S, LBO = 128) by GEMM1 and MN-major
-// along n (K = m, LBO = S, SBO = 128) by GEMM2.
-__device__ __forceinline__ int a_off(int m, int n, int S) {
-  return (m >> 3) * S + (n >> 3) * 128 + (m & 7) * 16 + (n & 7) * 2;
-}
-
-// Writes 8 values of this thread's tile row r at columns k0..k0+7 (k0 % 8 == 0) of a
-// K-major 128 x K operand, hi part at `hi`, lo part at `hi + 256 K`.
-__device__ __forceinline__ void put_operand8(unsigned char* hi, int K, int r, int k0,
-                                             const float (&v)[8]) {
-  uint4 h, l;
-  tc::split8(v, h, l);
-  int off = (r >> 3) * (K * 16) + (k0 >> 3) * 128 + (r & 7) * 16;
-  *reinterpret_cast<uint4*>(hi + off) = h;
-  *reinterpret_cast<uint4*>(hi + 256 * K + off) = l;
-}
+using tc::put_operand8;
+using tc::soft_thr;
 
 template <int NH, int MH>
 __global__ void __launch_bounds__(kTcThreads, 1) k_fista_tc(FtcParams p) {
@@ -79,15 +59,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_fista_tc(FtcParams p) {
   const int64_t pix = (int64_t)blockIdx.x * 128 + r;
   const bool valid = pix < p.P;
 
-  // A split into BF16 hi + lo (from FP64), zero padded to Mp x Np
-  for (int e = tid; e < Mp * Np; e += kTcThreads) {
-    int m = e / Np, n = e - m * Np;
-    double a = (m < M && n < N) ? p.A64[(size_t)m * N + n] : 0.0;
-    __nv_bfloat16 h = __float2bfloat16_rn((float)a);
-    __nv_bfloat16 l = __float2bfloat16_rn((float)(a - (double)__bfloat162float(h)));
-    *reinterpret_cast<__nv_bfloat16*>(sAh + a_off(m, n, S)) = h;
-    *reinterpret_cast<__nv_bfloat16*>(sAl + a_off(m, n, S)) = l;
-  }
+  // A (M x N) split into BF16 hi + lo (from FP64) in the dual layout, zero padded to
+  // Mp x Np: GEMM1 reads it K-major (A^T), GEMM2 MN-major
+  tc::stage_split(p.A64, M, N, Mp, Np, sAh, sAl);
   if (tid == 0) tc::mbar_init(&mbar, 1);
   if (warp == 0) tc::tmem_alloc(&tmem_slot, 512);
   tc::fence_async_smem();
@@ -183,16 +157,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_fista_tc(FtcParams p) {
     __syncthreads();
     tc::fence_after_sync();
     if (tid == 0) {
-      const uint32_t o = tc::smem_u32(sO), ah = tc::smem_u32(sAh), al = tc::smem_u32(sAl);
-      for (int s = 0; s < Mp / 16; ++s) {
-        uint64_t vh = tc::sdesc(o + s * 256, 128, Mp * 16);
-        uint64_t vl = tc::sdesc(o + 256 * Mp + s * 256, 128, Mp * 16);
-        uint64_t bh = tc::sdesc(ah + s * 2 * S, S, 128);
-        uint64_t bl = tc::sdesc(al + s * 2 * S, S, 128);
-        tc::mma_bf16(tR, vh, bh, id2, s > 0 ? 1u : 0u);
-        tc::mma_bf16(tR, vl, bh, id2, 1u);
-        tc::mma_bf16(tR, vh, bl, id2, 1u);
-      }
+      tc::split_product(tR, tc::smem_u32(sO), tc::smem_u32(sAh), tc::smem_u32(sAl), Mp, S,
+                        true, id2);
       tc::mma_commit(&mbar);
     }
     if (__syncthreads_or(!tc::mbar_wait(&mbar, phase, kWaitLimitNs))) {
@@ -231,16 +197,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_fista_tc(FtcParams p) {
     __syncthreads();
     tc::fence_after_sync();
     if (tid == 0) {
-      const uint32_t o = tc::smem_u32(sO), ah = tc::smem_u32(sAh), al = tc::smem_u32(sAl);
-      for (int s = 0; s < Np / 16; ++s) {
-        uint64_t xh = tc::sdesc(o + s * 256, 128, Np * 16);
-        uint64_t xl = tc::sdesc(o + 256 * Np + s * 256, 128, Np * 16);
-        uint64_t bh = tc::sdesc(ah + s * 256, 128, S);
-        uint64_t bl = tc::sdesc(al + s * 256, 128, S);
-        tc::mma_bf16(tR, xh, bh, id1, s > 0 ? 1u : 0u);
-        tc::mma_bf16(tR, xl, bh, id1, 1u);
-        tc::mma_bf16(tR, xh, bl, id1, 1u);
-      }
+      tc::split_product(tR, tc::smem_u32(sO), tc::smem_u32(sAh), tc::smem_u32(sAl), Np, S,
+                        false, id1);
       tc::mma_commit(&mbar);
     }
     if (__syncthreads_or(!tc::mbar_wait(&mbar, phase, kWaitLimitNs))) {

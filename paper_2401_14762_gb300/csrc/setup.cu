@@ -151,7 +151,7 @@ __global__ void __launch_bounds__(1024) k_lambda_max(int M, const double* S, dou
 // W = K^{-1} for the symmetric positive definite n x n matrix K (n <= 128), via the
 // Cholesky factor K = L L^T computed in place in `work`.  One CTA of 1024 threads.
 __global__ void __launch_bounds__(1024) k_spd_inverse(int n, const double* K, double* work,
-                                                      float* W, int* status) {
+                                                      float* W, double* W64, int* status) {
   const int tid = threadIdx.x, nt = blockDim.x;
   __shared__ int bad;
   if (tid == 0) bad = 0;
@@ -191,7 +191,10 @@ __global__ void __launch_bounds__(1024) k_spd_inverse(int n, const double* K, do
       for (int k = i + 1; k < n; ++k) s -= work[k * n + i] * y[k];
       y[i] = s / work[i * n + i];
     }
-    for (int i = 0; i < n; ++i) W[i * n + c] = (float)y[i];
+    for (int i = 0; i < n; ++i) {
+      W[i * n + c] = (float)y[i];
+      W64[i * n + c] = y[i];
+    }
   }
 }
 
@@ -250,7 +253,7 @@ cudaError_t setup_admm_factor(Ctx& c, double rho) {
   double *K = sc + M * N + N * N, *work = K + M * M;
   k_gemm_f64<<<nblk(M * M, 256), 256, 0, s>>>(M, M, N, c.A64, N, 1, c.A64, 1, N, K);
   k_add_diag<<<nblk(M, 256), 256, 0, s>>>(M, K, rho);
-  k_spd_inverse<<<1, 1024, 0, s>>>(M, K, work, c.W32, c.status);
+  k_spd_inverse<<<1, 1024, 0, s>>>(M, K, work, c.W32, c.W64, c.status);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   c.rho = rho;

@@ -133,5 +133,64 @@ __device__ __forceinline__ void split8(const float (&v)[8], uint4& hi, uint4& lo
   lo = make_uint4(l[0], l[1], l[2], l[3]);
 }
 
+// ---- 128-pixel tiles of the convex solvers ----
+
+// A K x N matrix B (row k, column n) in the dual layout: element (k, n) at
+// (k/8) S + (n/8) 128 + (k%8) 16 + (n%8) 2, S = 16 Np.  The MMAs read it MN-major as
+// the B operand of a product over k (LBO = S, SBO = 128) and K-major as the B operand
+// of a product over n, i.e. B^T (LBO = 128, SBO = S).
+__device__ __forceinline__ int dual_off(int k, int n, int S) {
+  return (k >> 3) * S + (n >> 3) * 128 + (k & 7) * 16 + (n & 7) * 2;
+}
+
+// Splits the FP64 matrix B (rows x cols, row-major) into BF16 hi + lo parts stored in the
+// dual layout at hi / lo, zero padded to rp x cp; all threads of the block take part.
+__device__ __forceinline__ void stage_split(const double* B, int rows, int cols, int rp, int cp,
+                                            unsigned char* hi, unsigned char* lo) {
+  const int S = 16 * cp;
+  for (int e = threadIdx.x; e < rp * cp; e += blockDim.x) {
+    int k = e / cp, n = e - k * cp;
+    double a = (k < rows && n < cols) ? B[(size_t)k * cols + n] : 0.0;
+    __nv_bfloat16 h = __float2bfloat16_rn((float)a);
+    __nv_bfloat16 l = __float2bfloat16_rn((float)(a - (double)__bfloat162float(h)));
+    *reinterpret_cast<__nv_bfloat16*>(hi + dual_off(k, n, S)) = h;
+    *reinterpret_cast<__nv_bfloat16*>(lo + dual_off(k, n, S)) = l;
+  }
+}
+
+// Writes 8 values of tile row r at columns k0..k0+7 (k0 % 8 == 0) of a K-major 128 x K
+// A operand (LBO = 128, SBO = 16 K), hi part at `hi`, lo part at `hi + 256 K`.
+__device__ __forceinline__ void put_operand8(unsigned char* hi, int K, int r, int k0,
+                                             const float (&v)[8]) {
+  uint4 h, l;
+  split8(v, h, l);
+  int off = (r >> 3) * (K * 16) + (k0 >> 3) * 128 + (r & 7) * 16;
+  *reinterpret_cast<uint4*>(hi + off) = h;
+  *reinterpret_cast<uint4*>(hi + 256 * K + off) = l;
+}
+
+// One product of the tile, issued by one thread: D = O B with the 128 x K operand O at
+// o (hi) / o + 256 K (lo) and B at bh / bl, as the three MMAs O_hi B_hi + O_lo B_hi +
+// O_hi B_lo (about 16 bits of each operand).  b_mn: B read MN-major (a product over the
+// dual layout's k, K-step stride 2 S) or K-major (over its n, K-step stride 256).
+__device__ __forceinline__ void split_product(uint32_t d_tmem, uint32_t o, uint32_t bh,
+                                              uint32_t bl, int K, int S, bool b_mn,
+                                              uint32_t idesc) {
+  for (int s = 0; s < K / 16; ++s) {
+    uint64_t ah = sdesc(o + s * 256, 128, K * 16);
+    uint64_t al = sdesc(o + 256 * K + s * 256, 128, K * 16);
+    uint64_t dh = b_mn ? sdesc(bh + s * 2 * S, S, 128) : sdesc(bh + s * 256, 128, S);
+    uint64_t dl = b_mn ? sdesc(bl + s * 2 * S, S, 128) : sdesc(bl + s * 256, 128, S);
+    mma_bf16(d_tmem, ah, dh, idesc, s > 0 ? 1u : 0u);
+    mma_bf16(d_tmem, al, dh, idesc, 1u);
+    mma_bf16(d_tmem, ah, dl, idesc, 1u);
+  }
+}
+
+__device__ __forceinline__ float soft_thr(float a, float t) {
+  float m = fabsf(a) - t;
+  return m > 0.f ? copysignf(m, a) : 0.f;
+}
+
 }  // namespace tc
 }  // namespace cs

@@ -1,10 +1,10 @@
 """Mixed-precision (tensor-core) path against the FP64 oracle.
 
-prec = CS_BF16 runs FISTA's two products on the tcgen05 tensor cores with split-BF16
-operands (hi*hi + lo*hi + hi*lo, FP32 accumulation).  The bar is relative L2 <= 1e-3
-against the FP64 oracle; at fixed, unconverged iteration counts on the ill-conditioned
-sparse case the FP32-path tolerance derived from the oracle's conditioning applies when
-it is looser.
+prec = CS_BF16 runs FISTA's two products (and ADMM's three, below) on the tcgen05 tensor
+cores with split-BF16 operands (hi*hi + lo*hi + hi*lo, FP32 accumulation).  The bar is
+relative L2 <= 1e-3 against the FP64 oracle; at fixed, unconverged iteration counts on
+the ill-conditioned sparse case the FP32-path tolerance derived from the oracle's
+conditioning applies when it is looser.
 """
 import numpy as np
 import pytest
@@ -84,3 +84,73 @@ def test_fista_bf16_stop_rule_and_edges(cs):
     Xb1, _, _ = gpu_run(cs.cs_recover_fista, ctx, pr.Y[:1], pr.N, 1e-3, 50, eps=0.0,
                         prec=cs.CS_BF16)
     assert rel_l2(Xb1, Xo1) <= REL_L2_MIXED
+
+
+# --------------------------------------------------------------------------- ADMM
+# prec = CS_BF16 runs ADMM's three products (A d, W e, A^T h) on the tensor cores with
+# split-BF16 operands where the tile fits in shared memory (N = 120 and 200 here); other
+# shapes run the FP32 path, which must meet the same bar.
+@pytest.mark.parametrize("shape,P,rho", [((80, 200), 32 * 20 + 7, 1.0),
+                                         ((48, 120), 300, 1.0),
+                                         ((48, 120), 300, 0.5),
+                                         ((90, 224), 200, 1.0)])
+def test_admm_bf16_powerlaw(cs, shape, P, rho):
+    M, N = shape
+    pr = Problem(M, N, P, "powerlaw", seed=3, noise_var=1e-3)
+    Xo, _ = orc.admm(pr.A, pr.Y, rho, 1e-3, 0.0, 300)
+    ctx = cs.cs_create(M, N, Phi=pr.Phi, admm_rho=rho)
+    Xb, it, cv = gpu_run(cs.cs_recover_admm, ctx, pr.Y, N, rho, 1e-3, 300, eps=0.0,
+                         prec=cs.CS_BF16)
+    Xf, _, _ = gpu_run(cs.cs_recover_admm, ctx, pr.Y, N, rho, 1e-3, 300, eps=0.0)
+    err, err32 = rel_l2(Xb, Xo), rel_l2(Xf, Xo)
+    print(f"admm bf16 {err:.2e} fp32 {err32:.2e}")
+    assert np.all(it == 300) and np.all(cv == 0)
+    assert err <= REL_L2_MIXED
+    if N in (120, 200):
+        assert not np.array_equal(Xb, Xf)  # the tensor-core path ran
+
+
+def test_admm_bf16_converged(cs):
+    # Delta = rho ||h - h_prev|| has a floor of about 2^-16 ||h|| on the split-BF16 path
+    # (~1e-6 here, ||h|| ~ ||y - A x|| / rho ~ 0.1), so the stop test uses eps = 1e-5
+    pr = Problem(48, 120, 200, "sparse", seed=21, S=6, noise_var=1e-4)
+    Xo, _ = orc.admm(pr.A, pr.Y, 1.0, 0.05, 0.0, 5000)
+    ctx = cs.cs_create(pr.M, pr.N, Phi=pr.Phi, admm_rho=1.0)
+    Xb, it, cv = gpu_run(cs.cs_recover_admm, ctx, pr.Y, pr.N, 1.0, 0.05, 5000, eps=1e-5,
+                         prec=cs.CS_BF16)
+    print(f"admm bf16 converged {rel_l2(Xb, Xo):.2e} iters {it.mean():.0f}")
+    assert np.all(cv == 1)
+    assert rel_l2(Xb, Xo) <= REL_L2_MIXED
+    assert np.all(support(Xb, 1e-3) == support(Xo, 1e-3))
+
+
+def test_admm_bf16_stop_rule_and_edges(cs):
+    """Delta stopping per pixel, eps > 1, zero iterations, a ragged single pixel."""
+    pr = Problem(80, 200, 129, "powerlaw", seed=4, noise_var=1e-3)
+    ctx = cs.cs_create(pr.M, pr.N, Phi=pr.Phi, admm_rho=1.0)
+    Xo, ito = orc.admm(pr.A, pr.Y, 1.0, 0.05, 1e-4, 3000)
+    Xb, it, cv = gpu_run(cs.cs_recover_admm, ctx, pr.Y, pr.N, 1.0, 0.05, 3000, eps=1e-4,
+                         prec=cs.CS_BF16)
+    assert np.all(cv == 1)
+    assert np.abs(it.astype(int) - ito.astype(int)).max() <= max(3, int(0.05 * ito.max()))
+    assert rel_l2(Xb, Xo) <= REL_L2_MIXED
+    Xb, it, _ = gpu_run(cs.cs_recover_admm, ctx, pr.Y, pr.N, 1.0, 0.05, 100, eps=2.0,
+                        prec=cs.CS_BF16)
+    assert np.all(Xb == 0) and np.all(it == 0)
+    Xb, it, _ = gpu_run(cs.cs_recover_admm, ctx, pr.Y, pr.N, 1.0, 0.05, 0, eps=0.0,
+                        prec=cs.CS_BF16)
+    assert np.all(Xb == 0) and np.all(it == 0)
+    Xo1, _ = orc.admm(pr.A, pr.Y[:1], 1.0, 1e-3, 0.0, 50)
+    Xb1, _, _ = gpu_run(cs.cs_recover_admm, ctx, pr.Y[:1], pr.N, 1.0, 1e-3, 50, eps=0.0,
+                        prec=cs.CS_BF16)
+    assert rel_l2(Xb1, Xo1) <= REL_L2_MIXED
+
+
+def test_admm_bf16_nonfinite_input_is_reported(cs):
+    pr = Problem(80, 200, 40, "powerlaw", seed=6, noise_var=1e-3)
+    Y = pr.Y.copy()
+    Y[7, 3] = np.nan
+    ctx = cs.cs_create(pr.M, pr.N, Phi=pr.Phi, admm_rho=1.0)
+    with pytest.raises(cs.CsError) as e:
+        gpu_run(cs.cs_recover_admm, ctx, Y, pr.N, 1.0, 1e-3, 20, eps=0.0, prec=cs.CS_BF16)
+    assert e.value.status == cs.CS_ERR_NONFINITE
