@@ -512,41 +512,35 @@ __device__ float topk_select_atoms(Warp& w, const float (&val)[kNK], int nvalid,
   return __uint_as_float(T);
 }
 
-// The k largest |vals[p]| over positions p < cnt (FP64, ties to the lower position),
-// by the same bitwise search on the 64-bit patterns.  Output in ascending position order.
+// The k largest |vals[p]| over positions p < cnt (FP64, ties to the lower position) by
+// rank counting: each position counts the positions that beat it -- a larger magnitude
+// (compared as IEEE bit patterns, which order like the values), or an equal one at a
+// lower position -- and is chosen when fewer than k do.  The order is total, so exactly
+// min(k, cnt) positions are chosen, NaN included.  Output in ascending position order.
 __device__ void topk_select_positions(Warp& w, const double* vals, int cnt, int k, int16_t* out) {
   const int lane = w.lane;
-  unsigned long long key[kNK];
-  bool ok[kNK];
-#pragma unroll
-  for (int kk = 0; kk < kNK; ++kk) {
-    int p = lane + 32 * kk;
-    ok[kk] = p < cnt;
-    key[kk] = ok[kk] ? (unsigned long long)__double_as_longlong(fabs(vals[p])) : 0ull;
-  }
-  unsigned long long T = 0;
-  for (int b = 63; b >= 0; --b) {
-    unsigned long long cand = T | (1ull << b);
-    unsigned c = 0;
-#pragma unroll
-    for (int kk = 0; kk < kNK; ++kk) c += (ok[kk] && key[kk] >= cand) ? 1u : 0u;
-    if (__reduce_add_sync(0xffffffffu, c) >= (unsigned)k) T = cand;
-  }
-  unsigned gt = 0;
-#pragma unroll
-  for (int kk = 0; kk < kNK; ++kk) gt += (ok[kk] && key[kk] > T) ? 1u : 0u;
-  const int need = k - (int)__reduce_add_sync(0xffffffffu, gt);
   const unsigned below = (1u << lane) - 1u;
-  int pos = 0, eq_before = 0;
-#pragma unroll
-  for (int kk = 0; kk < kNK; ++kk) {
-    bool isgt = ok[kk] && key[kk] > T, iseq = ok[kk] && key[kk] == T;
-    unsigned eqm = __ballot_sync(0xffffffffu, iseq);
-    bool take = isgt || (iseq && eq_before + __popc(eqm & below) < need);
-    unsigned tm = __ballot_sync(0xffffffffu, take);
-    if (take) out[pos + __popc(tm & below)] = (int16_t)(lane + 32 * kk);
-    pos += __popc(tm);
-    eq_before += __popc(eqm);
+  const unsigned long long mag = 0x7fffffffffffffffull;
+  int pos = 0;
+  for (int b0 = 0; b0 < cnt; b0 += 64) {  // two positions per lane per pass
+    const int p0 = b0 + lane, p1 = b0 + 32 + lane;
+    const unsigned long long k0 =
+        p0 < cnt ? (unsigned long long)__double_as_longlong(vals[p0]) & mag : 0ull;
+    const unsigned long long k1 =
+        p1 < cnt ? (unsigned long long)__double_as_longlong(vals[p1]) & mag : 0ull;
+    int r0 = 0, r1 = 0;
+    for (int i = 0; i < cnt; ++i) {
+      const unsigned long long ki = (unsigned long long)__double_as_longlong(vals[i]) & mag;
+      r0 += (ki > k0 || (ki == k0 && i < p0)) ? 1 : 0;
+      r1 += (ki > k1 || (ki == k1 && i < p1)) ? 1 : 0;
+    }
+    const bool t0 = p0 < cnt && r0 < k, t1 = p1 < cnt && r1 < k;
+    const unsigned m0 = __ballot_sync(0xffffffffu, t0);
+    if (t0) out[pos + __popc(m0 & below)] = (int16_t)p0;
+    pos += __popc(m0);
+    const unsigned m1 = __ballot_sync(0xffffffffu, t1);
+    if (t1) out[pos + __popc(m1 & below)] = (int16_t)p1;
+    pos += __popc(m1);
   }
   __syncwarp();
 }
@@ -965,7 +959,9 @@ __global__ void __launch_bounds__(256, 2) k_greedy(GrParams p) {
       }
       __syncwarp();
       nq = keep;  // q inherits c's ascending order
-      if (ALGO == kGomp && nq > 0) {
+      // the refit on q; when q is all of c (in c's order) it would repeat the solve just
+      // made, bit for bit, so x keeps that solution
+      if (ALGO == kGomp && nq > 0 && nq < nc) {
         fail |= !ls_solve<VR>(w, w.q, nq, w.Lq, w.invq, w.vq, w.sq, p.kmax);
         work += (double)nq * nq * nq / 3.0 + 2.0 * nq * nq;
         if (fail) break;
