@@ -10,6 +10,7 @@ FISTA 300 iterations (lambda = 1e-3), ADMM 300 iterations (rho = 1, lambda = 1e-
 gOMP kappa = 20, G = 4; BIHT kappa = 20, mu = 0.1; CoSaMP kappa = 20; eps = 1e-8.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+    python bench.py --only ALGO [--pixels P]     # one algorithm on P pixels, twice (profiling)
 
 Prints one JSON line.  value = recovered spectra per second over the whole job
 (pixels x algorithms per step / step time).  The FP64 oracle (CPU) is timed on a
@@ -417,6 +418,16 @@ def run_gpu(args):
                                 FP32_PEAK_TFLOPS}
         kernels["admm"]["precision"] = "split-BF16 tcgen05 (3 MMAs per product), FP32 acc"
         kernels["admm"]["speedup_vs_fp32"] = a32 / kern_ms["admm"]
+        # tensor-pipe view of the two tcgen05 kernels: MMA flops issued per pixel-iteration
+        # (3 split MMAs per product over the 16-padded shapes) against the measured BF16
+        # GEMM peak, sustained (both kernels run hundreds of iterations back to back)
+        Mp, Np = (M + 15) // 16 * 16, (N + 15) // 16 * 16
+        mma = {"fista": 3 * 2 * (2 * Mp * Np), "admm": 3 * 2 * (2 * Mp * Np + Mp * Mp)}
+        bf16 = pk.get("bf16_tflops_sustained")
+        for a, per in mma.items():
+            rate = per * its[a] / (kern_ms[a] * 1e-3) / 1e12
+            kernels[a]["mma_tflops"] = rate
+            kernels[a]["frac_bf16_sustained_of_measured"] = rate / bf16 if bf16 else None
         for a, (ms, same) in full_ms.items():
             kernels[a]["every_iteration_ms"] = ms
             kernels[a]["every_iteration_bitwise_equal"] = same
@@ -445,14 +456,56 @@ def run_gpu(args):
         dist.destroy_process_group()
 
 
+def run_only(args):
+    """One algorithm of the step on the first P pixels of the workload, called twice (the
+    first call is a warm-up), for kernel profiles; prints nothing but a short status."""
+    import torch
+
+    from paper_2401_14762_gb300 import build, cs
+    from paper_2401_14762_gb300 import synthetic as sy
+    build.build()
+    dev = torch.device("cuda", 0)
+    n = args.pixels
+    Phi = sy.gaussian_phi(M, N, SEED)
+    Xt = sy.powerlaw_coeffs_torch(n, N, SEED, dev)
+    E = sy.noise_torch(n, M, NOISE_VAR, SEED, dev)
+    ctx = cs.cs_create(M, N, Phi=Phi, admm_rho=RHO, stream=torch.cuda.current_stream().cuda_stream)
+    Y = torch.empty((n, M), device=dev)
+    cs.cs_measure(ctx, Xt, Y, E)
+    X = torch.empty((n, N), device=dev)
+    mixed = cs.make_opts(eps=EPS, prec=cs.CS_BF16)
+    calls = {
+        "measure": lambda: cs.cs_measure(ctx, Xt, Y, E),
+        "fista": lambda: cs.cs_recover_fista(ctx, Y, X, LAM, ITERS, mixed),
+        "fista_fp32": lambda: cs.cs_recover_fista(ctx, Y, X, LAM, ITERS, cs.make_opts(eps=EPS)),
+        "admm": lambda: cs.cs_recover_admm(ctx, Y, X, RHO, LAM, ITERS, mixed),
+        "admm_fp32": lambda: cs.cs_recover_admm(ctx, Y, X, RHO, LAM, ITERS, cs.make_opts(eps=EPS)),
+        "gomp": lambda: cs.cs_recover_gomp(ctx, Y, X, KAPPA, G, cs.make_opts(eps=EPS)),
+        "biht": lambda: cs.cs_recover_biht(ctx, Y, X, KAPPA, cs.make_opts(eps=EPS, mu=MU)),
+        "cosamp": lambda: cs.cs_recover_cosamp(ctx, Y, X, KAPPA, cs.make_opts(eps=EPS)),
+    }
+    for _ in range(2):
+        calls[args.only]()
+    cs.cs_sync(ctx)
+    torch.cuda.synchronize()
+    print(f"ok {args.only} {n} pixels", flush=True)
+    cs.cs_destroy(ctx)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--only", default=None,
+                    choices=["measure", "fista", "fista_fp32", "admm", "admm_fp32", "gomp",
+                             "biht", "cosamp"])
+    ap.add_argument("--pixels", type=int, default=16384)
     args = ap.parse_args()
-    if args.impl == "reference":
+    if args.only:
+        run_only(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_gpu(args)

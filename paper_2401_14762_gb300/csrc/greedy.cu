@@ -35,6 +35,7 @@ constexpr int kNK = kMaxN / 32;  // atoms per lane
 
 struct GrParams {
   int M, N, algo;
+  const double* A64;   // M x N
   const float* A32;    // M x N
   const float* At32;   // N x M
   const double* At64;  // N x M
@@ -66,7 +67,7 @@ struct GrParams {
 // sized for FP64 (the fallback factorisation then runs in place); otherwise they hold
 // the FP32 factors only and the fallback uses the warp's global slot.
 struct Layout {
-  int y, rf, r, xd, b, bflag, inc, c, q, sel, xq, L, invd, v, s, wv, Lq, invq, vq, sq,
+  int y, rf, r, xd, b, inc, c, q, sel, xq, L, invd, v, s, wv, Lq, invq, vq, sq,
       svals, cx, cq, ring, total;
   __host__ __device__ Layout(int M, int N, int cmax, int dmax, int kmax, bool fp64_smem,
                              bool need_q, bool need_cyc) {
@@ -95,14 +96,13 @@ struct Layout {
     cx = take(8 * kc, 8);
     ring = take(need_cyc ? 8 * 32 : 0, 8);  // hashes of the last 32 iterates
     r = take(8 * M, 8);
-    y = take(4 * M, 4);
+    y = take(8 * M, 8);
     rf = take(4 * M, 4);
     xd = take(4 * N, 4);
     c = take(2 * cmax, 2);
     q = take(2 * kmax, 2);
     cq = take(2 * kc, 2);
     sel = take(2 * N, 2);
-    bflag = take(N, 1);
     inc = take(N, 1);
     total = (o + 15) / 16 * 16;
   }
@@ -115,29 +115,38 @@ __device__ __forceinline__ int lidx(int t, int i, int cap) { return i * cap - i 
 struct Warp {
   const GrParams& p;
   int lane;
-  float *y, *rf, *xd;
-  double *r, *b, *xq, *L, *invd, *v, *s, *wv, *Lq, *invq, *vq, *sq, *svals;
-  uint8_t *bflag, *inc;
+  float *rf, *xd;
+  double *y, *r, *b, *xq, *L, *invd, *v, *s, *wv, *Lq, *invq, *vq, *sq, *svals;
+  uint8_t* inc;
   int16_t *c, *q, *sel;
   double* fb;  // this warp's global FP64 fallback slot, or nullptr
 };
 
-// (A^T y)_j in FP64, computed once per pixel and atom.
-__device__ double rhs(Warp& w, int j) {
-  if (!w.bflag[j]) {  // warp-uniform
-    const double* a = w.p.At64 + (size_t)j * w.p.M;
-    double part = 0.0;
-    for (int m = w.lane; m < w.p.M; m += 32) part += a[m] * (double)w.y[m];
-    part = warp_sum(part);
-    __syncwarp();
-    if (w.lane == 0) {
-      w.b[j] = part;
-      w.bflag[j] = 1;
+// (A^T y)_j in FP64, computed for every atom when the pixel starts (load_rhs).
+__device__ __forceinline__ double rhs(Warp& w, int j) { return w.b[j]; }
+
+// b = A^T y in FP64 for every atom: lanes own atoms, rows of A are read coalesced, and
+// each b_j sums its M products in the order m = 0, 1, ...
+__device__ void load_rhs(Warp& w) {
+  const int N = w.p.N, M = w.p.M;
+  double acc[kNK];
+#pragma unroll
+  for (int kk = 0; kk < kNK; ++kk) acc[kk] = 0.0;
+  for (int m = 0; m < M; ++m) {
+    const double ym = w.y[m];
+    const double* arow = w.p.A64 + (size_t)m * N;
+#pragma unroll
+    for (int kk = 0; kk < kNK; ++kk) {
+      const int n = w.lane + 32 * kk;
+      if (n < N) acc[kk] = fma(__ldg(arow + n), ym, acc[kk]);
     }
-    __syncwarp();
-    return part;
   }
-  return w.b[j];
+#pragma unroll
+  for (int kk = 0; kk < kNK; ++kk) {
+    const int n = w.lane + 32 * kk;
+    if (n < N) w.b[n] = acc[kk];
+  }
+  __syncwarp();
 }
 
 // Appends row n to the factor L of a growing normal-equation system.  g(t) gives the
@@ -223,24 +232,9 @@ __device__ __forceinline__ double warp_max(double v) {
   return v;
 }
 
-// (A^T y)_j in FP64 for every atom of atoms[0..n) into out[0..n); lanes take atoms, so
-// no reductions are needed; values are cached per pixel.
+// (A^T y)_j for every atom of atoms[0..n) into out[0..n).
 __device__ void fill_rhs(Warp& w, const int16_t* atoms, int n, double* out) {
-  const int M = w.p.M;
-  for (int t = w.lane; t < n; t += 32) {
-    int a = atoms[t];
-    double v;
-    if (w.bflag[a]) {
-      v = w.b[a];
-    } else {
-      const double* col = w.p.At64 + (size_t)a * M;
-      v = 0.0;
-      for (int m = 0; m < M; ++m) v += col[m] * (double)w.y[m];
-      w.b[a] = v;
-      w.bflag[a] = 1;
-    }
-    out[t] = v;
-  }
+  for (int t = w.lane; t < n; t += 32) out[t] = w.b[atoms[t]];
   __syncwarp();
 }
 
@@ -710,7 +704,7 @@ __device__ bool ls_min_norm(Warp& w, const int16_t* atoms, int n, double* s) {
           }
           return h;
         },
-        (double)w.y[k]);
+        w.y[k]);
     if (!ok) return false;
   }
   double* zv = w.svals;  // z = H^{-1} y
@@ -753,7 +747,7 @@ __global__ void __launch_bounds__(256, 2) k_greedy(GrParams p) {
   Layout lay(M, N, p.cmax, p.dmax, p.kmax, p.fb64 == nullptr, ALGO == kGomp, ALGO != kGomp);
   unsigned char* base = gsm + (size_t)wid * p.warp_bytes;
   Warp w{p, lane};
-  w.y = (float*)(base + lay.y);
+  w.y = (double*)(base + lay.y);
   w.rf = (float*)(base + lay.rf);
   w.r = (double*)(base + lay.r);
   w.xd = (float*)(base + lay.xd);
@@ -772,7 +766,6 @@ __global__ void __launch_bounds__(256, 2) k_greedy(GrParams p) {
   double* const cyc_x = (double*)(base + lay.cx);
   int16_t* const cyc_q = (int16_t*)(base + lay.cq);
   unsigned long long* const ring = (unsigned long long*)(base + lay.ring);
-  w.bflag = base + lay.bflag;
   w.inc = base + lay.inc;
   w.c = (int16_t*)(base + lay.c);
   w.q = (int16_t*)(base + lay.q);
@@ -781,7 +774,6 @@ __global__ void __launch_bounds__(256, 2) k_greedy(GrParams p) {
 
   for (int n = lane; n < N; n += 32) {
     w.xd[n] = 0.f;
-    w.bflag[n] = 0;
     w.inc[n] = 0;
   }
   // largest column norm of A (diagonal of the Gram matrix), for the FP32 error bound of
@@ -819,6 +811,7 @@ __global__ void __launch_bounds__(256, 2) k_greedy(GrParams p) {
     if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(p.status, kStNonFinite);
     double rnorm = sqrt(warp_sum(r2));  // ||r||_2, FP64
     __syncwarp();
+    if (!p.start_done && cap > 0) load_rhs(w);
 
     int nc = 0, nq = 0, it = 0;
     uint8_t conv = 0;
@@ -1000,7 +993,7 @@ __global__ void __launch_bounds__(256, 2) k_greedy(GrParams p) {
         for (int kk = 0; kk < 4; ++kk) {
           const int m = lane + 32 * kk;
           if (m < M) {
-            double rn = (double)w.y[m] - acc[kk];
+            double rn = w.y[m] - acc[kk];
             double df = rn - w.r[m];
             d2 += df * df;
             rr += rn * rn;
@@ -1069,7 +1062,6 @@ __global__ void __launch_bounds__(256, 2) k_greedy(GrParams p) {
     for (int n = lane; n < N; n += 32) {
       p.X[pix * N + n] = w.xd[n];
       w.xd[n] = 0.f;
-      w.bflag[n] = 0;
       w.inc[n] = 0;
     }
     if (lane == 0) {
@@ -1098,6 +1090,7 @@ cudaError_t launch_greedy(Ctx& c, GreedyAlgo algo, const GreedyArgs& a) {
   p.M = c.M;
   p.N = c.N;
   p.algo = algo;
+  p.A64 = c.A64;
   p.A32 = c.A32;
   p.At32 = c.At32;
   p.At64 = c.At64;
@@ -1295,6 +1288,7 @@ cudaError_t launch_gomp_noalloc(const double* A64, int M, int N, const GreedyArg
   p.M = M;
   p.N = N;
   p.algo = kGomp;
+  p.A64 = A64;
   p.A32 = A32;
   p.At32 = At32;
   p.At64 = At64;
