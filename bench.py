@@ -46,7 +46,7 @@ SM_COUNT, SM_MAX_MHZ = 152, 2070.0
 # FP32: 128 FMA lanes per SM; FP64: 1.25 TFLOP/s for the chip at the maximum clock.
 FP32_PEAK_TFLOPS = SM_COUNT * 128 * 2 * SM_MAX_MHZ * 1e6 / 1e12
 FP64_PEAK_TFLOPS = 1.25
-KERNEL_FILES = {"fista": "convex_f32.cu", "admm": "convex_f32.cu", "measure": "convex_f32.cu",
+KERNEL_FILES = {"fista": "fista_tc.cu", "admm": "admm_tc.cu", "measure": "convex_f32.cu",
                 "gomp": "greedy.cu", "biht": "greedy.cu", "cosamp": "greedy.cu"}
 
 
