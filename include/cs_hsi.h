@@ -177,6 +177,53 @@ cs_status cs_recover_gomp_noalloc(const double *A_dev, int M, int N, const float
                                   int64_t P, int kappa, int G, const cs_opts *opts,
                                   void *stream);
 
+/* ---- Batches: several cubes, each with its own dictionary, in one call ---- */
+
+typedef enum {
+  CS_ALGO_FISTA = 0,
+  CS_ALGO_ADMM = 1,
+  CS_ALGO_GOMP = 2,
+  CS_ALGO_BIHT = 3,
+  CS_ALGO_COSAMP = 4
+} cs_algo;
+
+/* One cube of a batch.  Y, X and the optional per-pixel arrays are device pointers the
+ * caller owns, in the layouts of the single-cube calls. */
+typedef struct {
+  cs_ctx *ctx;                    /* the cube's dictionary (its M and N), from cs_create */
+  const float *Y;                 /* P x M */
+  float *X;                       /* P x N */
+  int64_t P;
+  const int16_t *kappa_per_pixel; /* optional, greedy: per-pixel sparsity (<= params.kappa) */
+  int32_t *iters_out;             /* optional, P entries */
+  uint8_t *converged_out;         /* optional, P entries */
+} cs_batch_item;
+
+/* The algorithm's parameters, shared by every cube of the batch. */
+typedef struct {
+  double lambda; /* FISTA, ADMM */
+  double rho;    /* ADMM */
+  int iters;     /* FISTA, ADMM */
+  int kappa;     /* gOMP, BIHT, CoSaMP: sparsity, or the bound of kappa_per_pixel */
+  int G;         /* gOMP: atoms per iteration; 0 = max(1, floor(kappa_p / 5)) per pixel */
+} cs_algo_params;
+
+/* Recovers the n_items cubes with one algorithm (the paper's per-pixel problem, Section
+ * II, on every pixel of every cube).  The cubes may differ in M, N (each within the
+ * context limits), P and per-pixel sparsity.  gOMP, BIHT and CoSaMP run every cube in one
+ * persistent launch: warps take pixels from one counter over all cubes' pixels, so cubes
+ * and pixels that finish early free their warps for the rest.  FISTA and ADMM, whose
+ * per-pixel work is fixed by the iteration count, run one launch per cube.  Results
+ * equal the single-cube calls' bit for bit.
+ * opts gives eps, max_iters, prec, mu and cycle_skip for every cube; its per-pixel
+ * pointers are ignored (each item has its own).  Everything runs, asynchronously, on
+ * items[0].ctx's stream; device-side conditions of the whole batch latch in items[0].ctx's
+ * status word (cs_sync(items[0].ctx)).  Every context must be on the current device.
+ * Argument errors (a NULL or host pointer, P < 0, kappa out of any cube's range) return
+ * before anything is launched. */
+cs_status cs_recover_batch(const cs_batch_item *items, int n_items, cs_algo algo,
+                           const cs_algo_params *params, const cs_opts *opts);
+
 /* Waits for the context's stream and returns (and clears) the latched device status. */
 cs_status cs_sync(cs_ctx *ctx);
 

@@ -22,13 +22,25 @@ CS_FP32, CS_BF16, CS_FP8_E4M3 = 0, 1, 2
 EXPORTED = ["cs_opts_default", "cs_create", "cs_destroy", "cs_get_lipschitz", "cs_get_dictionary",
             "cs_measure", "cs_recover_fista", "cs_recover_admm", "cs_recover_gomp",
             "cs_recover_biht", "cs_recover_cosamp", "cs_get_work", "cs_recover_gomp_noalloc",
-            "cs_sync", "cs_last_error"]
+            "cs_recover_batch", "cs_sync", "cs_last_error"]
+CS_ALGO_FISTA, CS_ALGO_ADMM, CS_ALGO_GOMP, CS_ALGO_BIHT, CS_ALGO_COSAMP = 0, 1, 2, 3, 4
 
 
 class CsError(RuntimeError):
     def __init__(self, status: int, msg: str):
         super().__init__(f"cs status {status}: {msg}")
         self.status = status
+
+
+class cs_batch_item(ctypes.Structure):
+    _fields_ = [("ctx", ctypes.c_void_p), ("Y", ctypes.c_void_p), ("X", ctypes.c_void_p),
+                ("P", ctypes.c_int64), ("kappa_per_pixel", ctypes.c_void_p),
+                ("iters_out", ctypes.c_void_p), ("converged_out", ctypes.c_void_p)]
+
+
+class cs_algo_params(ctypes.Structure):
+    _fields_ = [("lambda_", ctypes.c_double), ("rho", ctypes.c_double), ("iters", ctypes.c_int),
+                ("kappa", ctypes.c_int), ("G", ctypes.c_int)]
 
 
 class cs_opts(ctypes.Structure):
@@ -67,6 +79,8 @@ def load_library(path: str = LIB_PATH):
     lib.cs_recover_cosamp.argtypes = [vp, vp, vp, i64, i32, op]
     lib.cs_get_work.argtypes = [vp, ctypes.POINTER(dbl)]
     lib.cs_recover_gomp_noalloc.argtypes = [vp, i32, i32, vp, vp, i64, i32, i32, op, vp]
+    lib.cs_recover_batch.argtypes = [ctypes.POINTER(cs_batch_item), i32, i32,
+                                     ctypes.POINTER(cs_algo_params), op]
     lib.cs_sync.argtypes = [vp]
     lib.cs_last_error.argtypes = []
     lib.cs_last_error.restype = ctypes.c_char_p
@@ -225,6 +239,25 @@ def cs_recover_gomp(ctx: Context, Y, X, kappa, G, opts: cs_opts | None = None, P
                                           int(P), int(kappa), int(G),
                                           ctypes.byref(opts) if opts else None))
     return X
+
+
+def cs_recover_batch(items, algo, lam=0.0, rho=1.0, iters=0, kappa=0, G=0,
+                     opts: cs_opts | None = None):
+    """Recovers several cubes with one algorithm (one launch for the greedy methods).
+    items: sequence of dicts with keys ctx, Y, X and optionally kappa_per_pixel, iters_out,
+    converged_out (device tensors).  Runs on items[0]'s context stream."""
+    arr = (cs_batch_item * len(items))()
+    for i, it in enumerate(items):
+        arr[i].ctx = it["ctx"].handle
+        arr[i].Y = _ptr(it["Y"], np.float32)
+        arr[i].X = _ptr(it["X"], np.float32)
+        arr[i].P = int(it.get("P", _rows(it["Y"])))
+        arr[i].kappa_per_pixel = _ptr(it.get("kappa_per_pixel"), np.int16)
+        arr[i].iters_out = _ptr(it.get("iters_out"), np.int32)
+        arr[i].converged_out = _ptr(it.get("converged_out"), np.uint8)
+    prm = cs_algo_params(float(lam), float(rho), int(iters), int(kappa), int(G))
+    _check(load_library().cs_recover_batch(arr, len(items), int(algo), ctypes.byref(prm),
+                                           ctypes.byref(opts) if opts else None))
 
 
 def cs_recover_biht(ctx: Context, Y, X, kappa, opts: cs_opts | None = None, P=None):

@@ -4,6 +4,7 @@
 #include <stdio.h>
 
 #include <cmath>
+#include <vector>
 #include <new>
 #include <string>
 
@@ -46,6 +47,7 @@ void free_ctx(Ctx& c) {
   cudaFree(c.At32);
   cudaFree(c.W32);
   cudaFree(c.W64);
+  cudaFree(c.cube_table);
   cudaFree(c.scratch64);
   cudaFree(c.status);
   cudaFree(c.counter);
@@ -337,6 +339,92 @@ cs_status cs_recover_biht(cs_ctx* ctx, const float* Y, float* X, int64_t P, int 
 cs_status cs_recover_cosamp(cs_ctx* ctx, const float* Y, float* X, int64_t P, int kappa,
                             const cs_opts* opts) {
   return greedy(ctx, cs::kCosamp, Y, X, P, kappa, 0, opts);
+}
+
+cs_status cs_recover_batch(const cs_batch_item* items, int n_items, cs_algo algo,
+                           const cs_algo_params* params, const cs_opts* opts) {
+  if (!items || n_items < 1) return arg_error("items is NULL or n_items < 1");
+  if (!params) return arg_error("params is NULL");
+  if (algo < CS_ALGO_FISTA || algo > CS_ALGO_COSAMP) return arg_error("unknown algorithm");
+  cs_opts o;
+  cs_opts_default(&o);
+  if (opts) o = *opts;
+  o.iters_out = nullptr;  // per item instead
+  o.converged_out = nullptr;
+  o.kappa_per_pixel = nullptr;
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return cuda_fail(cudaErrorNoDevice, "cudaGetDevice");
+  }
+  const bool greedy = algo >= CS_ALGO_GOMP;
+  const int kappa = params->kappa, G = params->G;
+  for (int i = 0; i < n_items; ++i) {
+    const cs_batch_item& it = items[i];
+    if (cs_status s = check_common(it.ctx, it.Y, it.X, it.P, &o)) return s;
+    const cs::Ctx& c = it.ctx->c;
+    if (c.device != dev) return arg_error("every context must be on the current device");
+    if (it.P > 0 && (!cs::is_device_ptr(it.Y) || !cs::is_device_ptr(it.X)))
+      return arg_error("batch cubes must be in device memory");
+    if ((it.iters_out && !cs::is_device_ptr(it.iters_out)) ||
+        (it.converged_out && !cs::is_device_ptr(it.converged_out)) ||
+        (it.kappa_per_pixel && !cs::is_device_ptr(it.kappa_per_pixel)))
+      return arg_error("per-pixel arrays must be device memory");
+    if (greedy && it.P > 0) {
+      if (kappa < 0 || kappa > c.N) return arg_error("kappa out of range for a cube");
+      if (algo == CS_ALGO_COSAMP && 2 * kappa > c.N)
+        return arg_error("CoSaMP needs 2 kappa <= N for every cube");
+      if (algo == CS_ALGO_GOMP && (G < 0 || G > c.N || (G == 0 && !it.kappa_per_pixel)))
+        return arg_error("G must be in 1..N (0 only with kappa_per_pixel)");
+    }
+  }
+  if (greedy && algo == CS_ALGO_BIHT && !std::isfinite(o.mu)) return arg_error("mu must be finite");
+  if (!greedy) {
+    if (!(params->lambda >= 0.0) || !std::isfinite(params->lambda))
+      return arg_error("lambda must be >= 0");
+    if (params->iters < 0) return arg_error("iters < 0");
+    if (algo == CS_ALGO_ADMM && (!(params->rho > 0.0) || !std::isfinite(params->rho)))
+      return arg_error("rho must be > 0");
+  }
+  cs::Ctx& c0 = items[0].ctx->c;
+  if (greedy) {
+    std::vector<cs::GreedyCube> cubes(n_items);
+    for (int i = 0; i < n_items; ++i) {
+      const cs_batch_item& it = items[i];
+      cubes[i] = cs::GreedyCube{&it.ctx->c, it.Y,          it.X,         it.P,
+                                it.kappa_per_pixel, it.iters_out, it.converged_out};
+    }
+    const cs::GreedyAlgo ga =
+        algo == CS_ALGO_GOMP ? cs::kGomp : (algo == CS_ALGO_BIHT ? cs::kBiht : cs::kCosamp);
+    cs::GreedyArgs a{nullptr, nullptr, 0, kappa, algo == CS_ALGO_GOMP ? G : 0, o.mu, o.eps,
+                     o.max_iters, nullptr, kappa, nullptr, nullptr, o.prec, o.cycle_skip != 0};
+    cudaError_t e = cs::launch_greedy_batch(c0, ga, cubes.data(), n_items, a);
+    if (e != cudaSuccess) return cuda_fail(e, "batched greedy launch");
+    return CS_OK;
+  }
+  // FISTA / ADMM: one launch per cube on items[0]'s stream, conditions in its status word
+  for (int i = 0; i < n_items; ++i) {
+    const cs_batch_item& it = items[i];
+    if (it.P == 0) continue;
+    cs::Ctx& c = it.ctx->c;
+    cudaStream_t own_stream = c.stream;
+    int* own_status = c.status;
+    c.stream = c0.stream;
+    c.status = c0.status;
+    cudaError_t e = cudaSuccess;
+    cs::ConvexArgs a{it.Y, it.X, it.P, params->lambda, params->rho, o.eps, params->iters,
+                     it.iters_out, it.converged_out, o.prec};
+    if (algo == CS_ALGO_ADMM) {
+      if (c.rho != params->rho) e = cs::setup_admm_factor(c, params->rho);
+      if (e == cudaSuccess) e = cs::launch_admm(c, a);
+    } else {
+      e = cs::launch_fista(c, a);
+    }
+    c.stream = own_stream;
+    c.status = own_status;
+    if (e != cudaSuccess) return cuda_fail(e, "batched convex launch");
+  }
+  return CS_OK;
 }
 
 cs_status cs_recover_gomp_noalloc(const double* A_dev, int M, int N, const float* Y, float* X,

@@ -50,6 +50,8 @@ struct Ctx {
   double* work = nullptr;     // algorithmic flops of the last greedy call (device, 1 entry)
   float* beta = nullptr;      // FISTA momentum weights (device), capacity beta_cap
   int beta_cap = 0;
+  void* cube_table = nullptr; // greedy launches' cube descriptors (device), cube_cap entries
+  int cube_cap = 0;
   size_t fb64_elems = 0;
   float* stage_in = nullptr;  // staging for host-pointer calls
   float* stage_out = nullptr;
@@ -107,6 +109,20 @@ struct GreedyArgs {
   bool cycle_skip;  // BIHT/CoSaMP: stop at a repeated iterate (exact, see k_greedy)
 };
 cudaError_t launch_greedy(Ctx& c, GreedyAlgo algo, const GreedyArgs& a);
+// One cube of a batched greedy launch (device pointers; Y/X/kappa/iters/conv per cube).
+struct GreedyCube {
+  const Ctx* ctx;
+  const float* Y;
+  float* X;
+  int64_t P;
+  const int16_t* kappa_pp;
+  int32_t* iters_out;
+  uint8_t* conv_out;
+};
+// All cubes in one persistent launch on c0's stream (its counter, status and slots);
+// a's Y, X, P and per-pixel pointers are unused.
+cudaError_t launch_greedy_batch(Ctx& c0, GreedyAlgo algo, const GreedyCube* cubes, int n,
+                                const GreedyArgs& a);
 
 // ---- allocation-free gOMP (scratch in a static device array) ----
 size_t noalloc_scratch_bytes(int M, int N);

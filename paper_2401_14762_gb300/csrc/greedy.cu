@@ -25,6 +25,7 @@
 #include <cuda_runtime.h>
 
 #include <mutex>
+#include <vector>
 
 #include "cs_internal.cuh"
 
@@ -33,19 +34,29 @@ namespace {
 
 constexpr int kNK = kMaxN / 32;  // atoms per lane
 
-struct GrParams {
-  int M, N, algo;
+// One cube of a launch: its dictionary data and its pixels, which are the launch's
+// pixels [pix0, pix0 + P).
+struct GrCube {
+  int M, N;
   const double* A64;   // M x N
   const float* A32;    // M x N
-  const float* At32;   // N x M
   const double* At64;  // N x M
   const double* G64;   // N x N
   const float* G32;    // N x N FP32 rounding of G64, or nullptr (gathers then convert)
   const float* Y;
   float* X;
-  int64_t P;
-  int kappa, G;
+  int64_t P, pix0;
   const int16_t* kappa_pp;
+  int32_t* iters_out;
+  uint8_t* conv_out;
+};
+
+struct GrParams {
+  int Mmax, Nmax, algo;  // the shared-memory slices are laid out for the largest cube
+  const GrCube* cubes;   // device table, ascending pix0
+  int ncubes;
+  int64_t total;         // pixels over all cubes
+  int kappa, G;
   float mu;
   double mu64;
   double eps2;
@@ -53,8 +64,6 @@ struct GrParams {
   int max_iters;
   int cmax, dmax, kmax;
   int warp_bytes;
-  int32_t* iters_out;
-  uint8_t* conv_out;
   int* status;
   unsigned long long* counter;
   double* fb64;      // per-warp global FP64 fallback slots (nullptr: FP64 factors in smem)
@@ -115,6 +124,7 @@ __device__ __forceinline__ int lidx(int t, int i, int cap) { return i * cap - i 
 struct Warp {
   const GrParams& p;
   int lane;
+  const GrCube* cb;  // the cube of the pixel in hand (device table entry)
   float *rf, *xd;
   double *y, *r, *b, *xq, *L, *invd, *v, *s, *wv, *Lq, *invq, *vq, *sq, *svals;
   uint8_t* inc;
@@ -128,13 +138,13 @@ __device__ __forceinline__ double rhs(Warp& w, int j) { return w.b[j]; }
 // b = A^T y in FP64 for every atom: lanes own atoms, rows of A are read coalesced, and
 // each b_j sums its M products in the order m = 0, 1, ...
 __device__ void load_rhs(Warp& w) {
-  const int N = w.p.N, M = w.p.M;
+  const int N = w.cb->N, M = w.cb->M;
   double acc[kNK];
 #pragma unroll
   for (int kk = 0; kk < kNK; ++kk) acc[kk] = 0.0;
   for (int m = 0; m < M; ++m) {
     const double ym = w.y[m];
-    const double* arow = w.p.A64 + (size_t)m * N;
+    const double* arow = w.cb->A64 + (size_t)m * N;
 #pragma unroll
     for (int kk = 0; kk < kNK; ++kk) {
       const int n = w.lane + 32 * kk;
@@ -255,12 +265,12 @@ __device__ __forceinline__ int ridx(int i, int k) { return (i * (i + 1) >> 1) + 
 // original diagonal (FP32 would lose the factor).  invd ends up holding 1 / L(j, j).
 template <int VR>
 __device__ bool chol32(Warp& w, float* L, float* invd, int n, const int16_t* atoms) {
-  const int lane = w.lane, N = w.p.N;
+  const int lane = w.lane, N = w.cb->N;
   // gather: G row atoms[k] (read at the sorted atoms, a few sectors) into column k;
   // several columns of loads are in flight before their stores
   constexpr int kB = VR <= 2 ? 8 : 4;
-  const float* G32 = w.p.G32;
-  const double* G64 = w.p.G64;
+  const float* G32 = w.cb->G32;
+  const double* G64 = w.cb->G64;
   for (int k0 = 0; k0 < n; k0 += kB) {
     float g[kB][VR];
 #pragma unroll
@@ -390,8 +400,8 @@ __device__ void bwd32(const float* L, const float* invd, int n, float (&v)[VR], 
 template <int VR>
 __device__ bool refine32(Warp& w, const float* L, const float* invd, int n,
                          const int16_t* atoms, const double* b, double* s) {
-  const int lane = w.lane, N = w.p.N;
-  const double* G = w.p.G64;
+  const int lane = w.lane, N = w.cb->N;
+  const double* G = w.cb->G64;
   double sr[VR], rr[VR];
 #pragma unroll
   for (int k = 0; k < VR; ++k) {
@@ -651,8 +661,8 @@ __device__ void certify_topk(Warp& w, const float (&val)[kNK], int nvalid, int k
 // Fresh factorisation of the normal equations on atoms[0..n) and solve into s.
 __device__ bool ls_fresh(Warp& w, const int16_t* atoms, int n, double* L, double* invd, double* v,
                          double* s, int cap) {
-  const double* G = w.p.G64;
-  const int N = w.p.N;
+  const double* G = w.cb->G64;
+  const int N = w.cb->N;
   bool ok = true;
   for (int k = 0; k < n; ++k) {
     const double* grow = G + (size_t)atoms[k] * N;
@@ -684,8 +694,8 @@ __device__ bool ls_solve(Warp& w, const int16_t* atoms, int n, double* Lbuf, dou
 
 // Minimum-norm solution for |c| > M: s = A_c^T H^{-1} y with H = A_c A_c^T (M x M).
 __device__ bool ls_min_norm(Warp& w, const int16_t* atoms, int n, double* s) {
-  const int M = w.p.M;
-  const double* At = w.p.At64;
+  const int M = w.cb->M;
+  const double* At = w.cb->At64;
   // FP64 M x M factor: the warp's global slot (dmax = M here), else the FP64-sized smem
   double* L = w.fb ? w.fb : w.L;
   double* invd = w.fb ? w.fb + M * (M + 1) / 2 : w.invd;
@@ -743,10 +753,10 @@ template <int ALGO, int VR>
 __global__ void __launch_bounds__(256, 2) k_greedy(GrParams p) {
   extern __shared__ __align__(16) unsigned char gsm[];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const int M = p.M, N = p.N;
-  Layout lay(M, N, p.cmax, p.dmax, p.kmax, p.fb64 == nullptr, ALGO == kGomp, ALGO != kGomp);
+  Layout lay(p.Mmax, p.Nmax, p.cmax, p.dmax, p.kmax, p.fb64 == nullptr, ALGO == kGomp,
+             ALGO != kGomp);
   unsigned char* base = gsm + (size_t)wid * p.warp_bytes;
-  Warp w{p, lane};
+  Warp w{p, lane, p.cubes};
   w.y = (double*)(base + lay.y);
   w.rf = (float*)(base + lay.rf);
   w.r = (double*)(base + lay.r);
@@ -772,26 +782,45 @@ __global__ void __launch_bounds__(256, 2) k_greedy(GrParams p) {
   w.sel = (int16_t*)(base + lay.sel);
   w.fb = p.fb64 ? p.fb64 + (size_t)(blockIdx.x * (blockDim.x >> 5) + wid) * p.fb_slot : nullptr;
 
-  for (int n = lane; n < N; n += 32) {
+  for (int n = lane; n < p.Nmax; n += 32) {
     w.xd[n] = 0.f;
     w.inc[n] = 0;
   }
-  // largest column norm of A (diagonal of the Gram matrix), for the FP32 error bound of
-  // the correlation
-  double cn2 = 0.0;
-  for (int n = lane; n < N; n += 32) cn2 = fmax(cn2, p.G64[(size_t)n * N + n]);
-  const double cnorm = sqrt(warp_max(cn2));
   __syncwarp();
+  int cur = -1;        // cube whose data w.cb holds
+  double cnorm = 0.0;  // its largest column norm
 
   for (;;) {
     unsigned long long pix_u = 0;
     if (lane == 0) pix_u = atomicAdd(p.counter, 1ull);
     pix_u = __shfl_sync(0xffffffffu, pix_u, 0);
-    if (pix_u >= (unsigned long long)p.P) break;
-    const int64_t pix = (int64_t)pix_u;
+    if (pix_u >= (unsigned long long)p.total) break;
+    // the pixel's cube: the last one starting at or before it (warp-uniform search)
+    int ci = 0;
+    if (p.ncubes > 1) {
+      int lo = 0, hi = p.ncubes - 1;
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if ((unsigned long long)p.cubes[mid].pix0 <= pix_u) lo = mid;
+        else hi = mid - 1;
+      }
+      ci = lo;
+    }
+    if (ci != cur) {
+      w.cb = p.cubes + ci;
+      cur = ci;
+      // largest column norm of A (diagonal of the Gram matrix), for the FP32 error bound
+      // of the correlation
+      double cn2 = 0.0;
+      for (int n = lane; n < w.cb->N; n += 32) cn2 = fmax(cn2, w.cb->G64[(size_t)n * w.cb->N + n]);
+      cnorm = sqrt(warp_max(cn2));
+    }
+    const GrCube& cb = *w.cb;
+    const int M = cb.M, N = cb.N;
+    const int64_t pix = (int64_t)pix_u - cb.pix0;
 
     // a per-pixel level outside 0..kappa bound is clamped: the workspace holds kmax atoms
-    const int kappa = p.kappa_pp ? min(max((int)p.kappa_pp[pix], 0), p.kmax) : p.kappa;
+    const int kappa = cb.kappa_pp ? min(max((int)cb.kappa_pp[pix], 0), p.kmax) : p.kappa;
     const int G = p.G > 0 ? p.G : (kappa / 5 > 1 ? kappa / 5 : 1);
     int cap = p.max_iters;
     if (ALGO == kGomp) {
@@ -801,7 +830,7 @@ __global__ void __launch_bounds__(256, 2) k_greedy(GrParams p) {
     bool bad = false;
     double r2 = 0.0;
     for (int m = lane; m < M; m += 32) {
-      float yv = p.Y[pix * M + m];
+      float yv = cb.Y[pix * M + m];
       bad |= !isfinite(yv);
       w.y[m] = yv;
       w.r[m] = (double)yv;  // r^0 = y
@@ -837,7 +866,7 @@ __global__ void __launch_bounds__(256, 2) k_greedy(GrParams p) {
 #pragma unroll 4
       for (int m = 0; m < M; ++m) {
         float rm = w.rf[m];
-        const float* arow = p.A32 + (size_t)m * N;
+        const float* arow = cb.A32 + (size_t)m * N;
 #pragma unroll
         for (int kk = 0; kk < kNK; ++kk) {
           int n = lane + 32 * kk;
@@ -875,7 +904,7 @@ __global__ void __launch_bounds__(256, 2) k_greedy(GrParams p) {
               p.mu64 * pbound + 0x1p-24 * 1.01 * ((double)um + xm + p.mu64 * cnorm * rnorm);
           certify_topk(w, val, N, ksel, tk, (float)(E * 1.001),
                        [&](int j) {
-                         const double* a = p.At64 + (size_t)j * M;
+                         const double* a = cb.At64 + (size_t)j * M;
                          double g = 0.0;
                          for (int m = 0; m < M; ++m) g += a[m] * w.r[m];
                          double xj = 0.0;
@@ -887,7 +916,7 @@ __global__ void __launch_bounds__(256, 2) k_greedy(GrParams p) {
         } else {
           certify_topk(w, val, N, ksel, tk, (float)(pbound * 1.001),
                        [&](int j) {
-                         const double* a = p.At64 + (size_t)j * M;
+                         const double* a = cb.At64 + (size_t)j * M;
                          double g = 0.0;
                          for (int m = 0; m < M; ++m) g += a[m] * w.r[m];
                          return g;
@@ -983,7 +1012,7 @@ __global__ void __launch_bounds__(256, 2) k_greedy(GrParams p) {
         const int mc = M - 1;
 #pragma unroll 4
         for (int j = 0; j < nq; ++j) {
-          const double* col = p.At64 + (size_t)w.q[j] * M;
+          const double* col = cb.At64 + (size_t)w.q[j] * M;
           const double xj = w.xq[j];
 #pragma unroll
           for (int kk = 0; kk < 4; ++kk)
@@ -1060,13 +1089,13 @@ __global__ void __launch_bounds__(256, 2) k_greedy(GrParams p) {
     }
     // output and reset
     for (int n = lane; n < N; n += 32) {
-      p.X[pix * N + n] = w.xd[n];
+      cb.X[pix * N + n] = w.xd[n];
       w.xd[n] = 0.f;
       w.inc[n] = 0;
     }
     if (lane == 0) {
-      if (p.iters_out) p.iters_out[pix] = it;
-      if (p.conv_out) p.conv_out[pix] = conv;
+      if (cb.iters_out) cb.iters_out[pix] = it;
+      if (cb.conv_out) cb.conv_out[pix] = conv;
       if (p.work) atomicAdd(p.work, work);
     }
     __syncwarp();
@@ -1084,56 +1113,111 @@ auto greedy_kernel(int vr) {
 
 }  // namespace
 
-cudaError_t launch_greedy(Ctx& c, GreedyAlgo algo, const GreedyArgs& a) {
-  if (a.P == 0) return cudaSuccess;
-  GrParams p{};
-  p.M = c.M;
-  p.N = c.N;
-  p.algo = algo;
-  p.A64 = c.A64;
-  p.A32 = c.A32;
-  p.At32 = c.At32;
-  p.At64 = c.At64;
-  p.G64 = c.G64;
-  p.G32 = c.G32;
-  p.Y = a.Y;
-  p.X = a.X;
-  p.P = a.P;
-  p.kappa = a.kappa;
-  p.G = a.G;
-  p.kappa_pp = a.kappa_pp;
-  p.mu = (float)a.mu;
-  p.mu64 = a.mu;
-  p.eps2 = a.eps * a.eps;
-  p.start_done = a.eps > 1.0;
-  p.max_iters = a.max_iters;
-  p.iters_out = a.iters_out;
-  p.conv_out = a.conv_out;
-  p.status = c.status;
-  p.counter = reinterpret_cast<unsigned long long*>(c.counter);
-  p.work = c.work;
-  p.cycle_skip = a.cycle_skip ? 1 : 0;
+namespace {
+
+// Cube entries reach the device table through kernel parameters (32 per launch), so a
+// call copies from no host memory and can be captured in a CUDA graph.
+constexpr int kCubesPerPut = 32;
+struct CubeBlock {
+  GrCube c[kCubesPerPut];
+  int n;
+};
+__global__ void k_put_cubes(CubeBlock b, GrCube* dst) {
+  if ((int)threadIdx.x < b.n) dst[threadIdx.x] = b.c[threadIdx.x];
+}
+cudaError_t put_cubes(const GrCube* host, int n, GrCube* dst, cudaStream_t s) {
+  for (int i0 = 0; i0 < n; i0 += kCubesPerPut) {
+    CubeBlock b{};
+    b.n = n - i0 < kCubesPerPut ? n - i0 : kCubesPerPut;
+    for (int i = 0; i < b.n; ++i) b.c[i] = host[i0 + i];
+    k_put_cubes<<<1, kCubesPerPut, 0, s>>>(b, dst + i0);
+  }
+  return cudaGetLastError();
+}
+
+GrCube cube_of(const Ctx& c, const float* Y, float* X, int64_t P, const int16_t* kappa_pp,
+               int32_t* iters_out, uint8_t* conv_out, int64_t pix0) {
+  GrCube g{};
+  g.M = c.M;
+  g.N = c.N;
+  g.A64 = c.A64;
+  g.A32 = c.A32;
+  g.At64 = c.At64;
+  g.G64 = c.G64;
+  g.G32 = c.G32;
+  g.Y = Y;
+  g.X = X;
+  g.P = P;
+  g.pix0 = pix0;
+  g.kappa_pp = kappa_pp;
+  g.iters_out = iters_out;
+  g.conv_out = conv_out;
+  return g;
+}
+
+// Support capacities of a launch (cmax atoms in c, dmax rows of an FP32 factor, kmax
+// kept atoms) for cubes of at most Mmax measurements and Nmax atoms.
+void capacities(GrParams& p, GreedyAlgo algo, const GreedyArgs& a, int Mmax, int Nmax) {
   const int K = a.kappa_max;
-  const int M = c.M, N = c.N;
   int cmax;
   if (algo == kGomp) {
     int gmax = a.G > 0 ? a.G : (K / 5 > 1 ? K / 5 : 1);
     int iters = a.max_iters < K ? a.max_iters : K;
     long long cm = (long long)gmax * (iters > 0 ? iters : 1);
-    cmax = (int)(cm < M ? cm : M);
-    if (a.G == 0) cmax = M;  // per-pixel G: bound by M
+    cmax = (int)(cm < Mmax ? cm : Mmax);
+    if (a.G == 0) cmax = Mmax;  // per-pixel G: bound by M
   } else if (algo == kCosamp) {
-    cmax = 3 * K < N ? 3 * K : N;
+    cmax = 3 * K < Nmax ? 3 * K : Nmax;
   } else {
-    cmax = 2 * K < N ? 2 * K : N;
+    cmax = 2 * K < Nmax ? 2 * K : Nmax;
   }
   if (cmax < 1) cmax = 1;
   p.cmax = cmax;
-  p.dmax = cmax < M ? cmax : M;
+  p.dmax = cmax < Mmax ? cmax : Mmax;
   p.kmax = K > 0 ? K : 1;
+}
+
+void scalars(GrParams& p, GreedyAlgo algo, const GreedyArgs& a) {
+  p.algo = algo;
+  p.kappa = a.kappa;
+  p.G = a.G;
+  p.mu = (float)a.mu;
+  p.mu64 = a.mu;
+  p.eps2 = a.eps * a.eps;
+  p.start_done = a.eps > 1.0;
+  p.max_iters = a.max_iters;
+  p.cycle_skip = a.cycle_skip ? 1 : 0;
+}
+
+// One persistent launch over the cubes host[0..n) (ascending pix0, total pixels), on the
+// context's stream, with its counter, work word, status word and fallback slots.
+cudaError_t run_greedy(Ctx& c, GreedyAlgo algo, const GreedyArgs& a, const GrCube* host, int n,
+                       int Mmax, int Nmax, int64_t total) {
+  if (c.cube_cap < n) {
+    cudaFree(c.cube_table);
+    c.cube_table = nullptr;
+    c.cube_cap = 0;
+    cudaError_t ea = cudaMalloc(&c.cube_table, sizeof(GrCube) * (size_t)n);
+    if (ea != cudaSuccess) return ea;
+    c.cube_cap = n;
+  }
+  GrCube* table = static_cast<GrCube*>(c.cube_table);
+  cudaError_t e = put_cubes(host, n, table, c.stream);
+  if (e != cudaSuccess) return e;
+  GrParams p{};
+  scalars(p, algo, a);
+  p.Mmax = Mmax;
+  p.Nmax = Nmax;
+  p.cubes = table;
+  p.ncubes = n;
+  p.total = total;
+  p.status = c.status;
+  p.counter = reinterpret_cast<unsigned long long*>(c.counter);
+  p.work = c.work;
+  capacities(p, algo, a, Mmax, Nmax);
   // FP32 factors in shared memory; the rare FP64 fallback (and the |c| > M minimum-norm
   // solve) use one global slot per resident warp, so more warps fit on an SM.
-  Layout lay(M, N, p.cmax, p.dmax, p.kmax, false, algo == kGomp, algo != kGomp);
+  Layout lay(Mmax, Nmax, p.cmax, p.dmax, p.kmax, false, algo == kGomp, algo != kGomp);
   p.warp_bytes = lay.total;
   // one CTA of up to 8 warps per SM, or two smaller ones if that seats more warps
   int warps1 = (220 * 1024) / lay.total, warps2 = (110 * 1024) / lay.total;
@@ -1143,7 +1227,7 @@ cudaError_t launch_greedy(Ctx& c, GreedyAlgo algo, const GreedyArgs& a) {
   if (warps < 1) warps = 1;
   if ((size_t)warps * lay.total > 220 * 1024) return cudaErrorInvalidConfiguration;
   size_t smem = (size_t)warps * lay.total;
-  cudaError_t e = cudaMemsetAsync(c.counter, 0, sizeof(unsigned long long), c.stream);
+  e = cudaMemsetAsync(c.counter, 0, sizeof(unsigned long long), c.stream);
   if (e == cudaSuccess && c.work) e = cudaMemsetAsync(c.work, 0, sizeof(double), c.stream);
   if (e != cudaSuccess) return e;
   auto launch = [&](auto kern) {
@@ -1152,7 +1236,7 @@ cudaError_t launch_greedy(Ctx& c, GreedyAlgo algo, const GreedyArgs& a) {
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, warps * 32, smem);
     if (per_sm < 1) per_sm = 1;
     long long grid = (long long)c.num_sms * per_sm;
-    long long need = (a.P + warps - 1) / warps;
+    long long need = (total + warps - 1) / warps;
     if (grid > need) grid = need;
     const int D = p.dmax;
     p.fb_slot = D * (D + 1) / 2 + 2 * D;
@@ -1173,6 +1257,32 @@ cudaError_t launch_greedy(Ctx& c, GreedyAlgo algo, const GreedyArgs& a) {
   if (algo == kGomp) return launch(greedy_kernel<kGomp>(vr));
   if (algo == kBiht) return launch(greedy_kernel<kBiht>(vr));
   return launch(greedy_kernel<kCosamp>(vr));
+}
+
+}  // namespace
+
+cudaError_t launch_greedy(Ctx& c, GreedyAlgo algo, const GreedyArgs& a) {
+  if (a.P == 0) return cudaSuccess;
+  GrCube cube = cube_of(c, a.Y, a.X, a.P, a.kappa_pp, a.iters_out, a.conv_out, 0);
+  return run_greedy(c, algo, a, &cube, 1, c.M, c.N, a.P);
+}
+
+cudaError_t launch_greedy_batch(Ctx& c0, GreedyAlgo algo, const GreedyCube* cubes, int n,
+                                const GreedyArgs& a) {
+  std::vector<GrCube> host;
+  host.reserve(n);
+  int64_t total = 0;
+  int Mmax = 1, Nmax = 1;
+  for (int i = 0; i < n; ++i) {
+    const GreedyCube& g = cubes[i];
+    if (g.P == 0) continue;
+    host.push_back(cube_of(*g.ctx, g.Y, g.X, g.P, g.kappa_pp, g.iters_out, g.conv_out, total));
+    total += g.P;
+    if (g.ctx->M > Mmax) Mmax = g.ctx->M;
+    if (g.ctx->N > Nmax) Nmax = g.ctx->N;
+  }
+  if (total == 0) return cudaSuccess;
+  return run_greedy(c0, algo, a, host.data(), (int)host.size(), Mmax, Nmax, total);
 }
 
 }  // namespace cs
@@ -1198,7 +1308,7 @@ namespace cs {
 namespace {
 
 struct NoAllocLayout {
-  size_t counter, status, A32, At32, At64, G64, total;
+  size_t counter, status, A32, At32, At64, G64, cube, total;
   NoAllocLayout(int M, int N) {
     size_t o = 0;
     auto take = [&](size_t bytes) {
@@ -1212,6 +1322,7 @@ struct NoAllocLayout {
     At32 = take(sizeof(float) * (size_t)M * N);
     At64 = take(sizeof(double) * (size_t)M * N);
     G64 = take(sizeof(double) * (size_t)N * N);
+    cube = take(sizeof(GrCube));
     total = o;
   }
 };
@@ -1284,40 +1395,34 @@ cudaError_t launch_gomp_noalloc(const double* A64, int M, int N, const GreedyArg
   int num_sms = 0;
   e = cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) return e;
+  GrCube cube{};
+  cube.M = M;
+  cube.N = N;
+  cube.A64 = A64;
+  cube.A32 = A32;
+  cube.At64 = At64;
+  cube.G64 = G64;
+  cube.G32 = nullptr;  // the factor gathers convert from G64
+  cube.Y = a.Y;
+  cube.X = a.X;
+  cube.P = a.P;
+  cube.pix0 = 0;
+  cube.kappa_pp = a.kappa_pp;
+  cube.iters_out = a.iters_out;
+  cube.conv_out = a.conv_out;
+  GrCube* table = reinterpret_cast<GrCube*>(s + lay.cube);
+  e = put_cubes(&cube, 1, table, stream);
+  if (e != cudaSuccess) return e;
   GrParams p{};
-  p.M = M;
-  p.N = N;
-  p.algo = kGomp;
-  p.A64 = A64;
-  p.A32 = A32;
-  p.At32 = At32;
-  p.At64 = At64;
-  p.G64 = G64;
-  p.Y = a.Y;
-  p.X = a.X;
-  p.P = a.P;
-  p.kappa = a.kappa;
-  p.G = a.G;
-  p.kappa_pp = a.kappa_pp;
-  p.mu = (float)a.mu;
-  p.mu64 = a.mu;
-  p.eps2 = a.eps * a.eps;
-  p.start_done = a.eps > 1.0;
-  p.max_iters = a.max_iters;
-  p.iters_out = a.iters_out;
-  p.conv_out = a.conv_out;
+  scalars(p, kGomp, a);
+  p.Mmax = M;
+  p.Nmax = N;
+  p.cubes = table;
+  p.ncubes = 1;
+  p.total = a.P;
   p.status = reinterpret_cast<int*>(s + lay.status);
   p.counter = reinterpret_cast<unsigned long long*>(s + lay.counter);
-  const int K = a.kappa_max;
-  int gmax = a.G > 0 ? a.G : (K / 5 > 1 ? K / 5 : 1);
-  int iters = a.max_iters < K ? a.max_iters : K;
-  long long cm = (long long)gmax * (iters > 0 ? iters : 1);
-  int cmax = (int)(cm < M ? cm : M);
-  if (a.G == 0) cmax = M;
-  if (cmax < 1) cmax = 1;
-  p.cmax = cmax;
-  p.dmax = cmax < M ? cmax : M;
-  p.kmax = K > 0 ? K : 1;
+  capacities(p, kGomp, a, M, N);
   Layout wl(M, N, p.cmax, p.dmax, p.kmax, true, true, false);
   p.warp_bytes = wl.total;
   int warps = (220 * 1024) / wl.total;
