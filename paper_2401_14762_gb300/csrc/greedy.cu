@@ -62,7 +62,7 @@ struct GrParams {
   double eps2;
   int start_done;
   int max_iters;
-  int cmax, dmax, kmax;
+  int cmax, dmax, kmax, selmax;
   int warp_bytes;
   int* status;
   unsigned long long* counter;
@@ -78,8 +78,8 @@ struct GrParams {
 struct Layout {
   int y, rf, r, xd, b, inc, c, q, sel, xq, L, invd, v, s, wv, Lq, invq, vq, sq,
       svals, cx, cq, ring, total;
-  __host__ __device__ Layout(int M, int N, int cmax, int dmax, int kmax, bool fp64_smem,
-                             bool need_q, bool need_cyc) {
+  __host__ __device__ Layout(int M, int N, int cmax, int dmax, int kmax, int selmax,
+                             bool fp64_smem, bool need_q, bool need_cyc, bool need_xd) {
     const int fw = fp64_smem ? 8 : 4;
     int o = 0;
     auto take = [&](int bytes, int align) {
@@ -91,13 +91,13 @@ struct Layout {
     b = take(8 * N, 8);
     xq = take(8 * kmax, 8);
     L = take(fw * (dmax * (dmax + 1) / 2), 8);
-    invd = take(8 * dmax, 8);
+    invd = take(fw * dmax, 8);
     v = take(8 * dmax, 8);
     s = take(8 * cmax, 8);
     wv = take(8 * dmax, 8);
     const int kq = need_q ? kmax : 0;
     Lq = take(fw * (kq * (kq + 1) / 2), 8);
-    invq = take(8 * kq, 8);
+    invq = take(fw * kq, 8);
     vq = take(8 * kq, 8);
     sq = take(8 * kq, 8);
     svals = take(8 * cmax, 8);
@@ -107,11 +107,11 @@ struct Layout {
     r = take(8 * M, 8);
     y = take(8 * M, 8);
     rf = take(4 * M, 4);
-    xd = take(4 * N, 4);
+    xd = take(need_xd ? 4 * N : 0, 4);  // FP32 x row (BIHT's u = x + mu A^T r)
     c = take(2 * cmax, 2);
     q = take(2 * kmax, 2);
     cq = take(2 * kc, 2);
-    sel = take(2 * N, 2);
+    sel = take(2 * selmax, 2);  // a selection: G, 2 kappa or kappa atoms, or kappa positions
     inc = take(N, 1);
     total = (o + 15) / 16 * 16;
   }
@@ -753,8 +753,8 @@ template <int ALGO, int VR>
 __global__ void __launch_bounds__(256, 2) k_greedy(GrParams p) {
   extern __shared__ __align__(16) unsigned char gsm[];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  Layout lay(p.Mmax, p.Nmax, p.cmax, p.dmax, p.kmax, p.fb64 == nullptr, ALGO == kGomp,
-             ALGO != kGomp);
+  Layout lay(p.Mmax, p.Nmax, p.cmax, p.dmax, p.kmax, p.selmax, p.fb64 == nullptr,
+             ALGO == kGomp, ALGO != kGomp, ALGO == kBiht);
   unsigned char* base = gsm + (size_t)wid * p.warp_bytes;
   Warp w{p, lane, p.cubes};
   w.y = (double*)(base + lay.y);
@@ -783,7 +783,7 @@ __global__ void __launch_bounds__(256, 2) k_greedy(GrParams p) {
   w.fb = p.fb64 ? p.fb64 + (size_t)(blockIdx.x * (blockDim.x >> 5) + wid) * p.fb_slot : nullptr;
 
   for (int n = lane; n < p.Nmax; n += 32) {
-    w.xd[n] = 0.f;
+    if (ALGO == kBiht) w.xd[n] = 0.f;
     w.inc[n] = 0;
   }
   __syncwarp();
@@ -965,7 +965,8 @@ __global__ void __launch_bounds__(256, 2) k_greedy(GrParams p) {
 
       // ---- step 3: prune to kappa (and refit for gOMP) ----
       // previous support leaves xd
-      for (int j = lane; j < nq; j += 32) w.xd[w.q[j]] = 0.f;
+      if (ALGO == kBiht)
+        for (int j = lane; j < nq; j += 32) w.xd[w.q[j]] = 0.f;
       __syncwarp();
       int keep = nc < kappa ? nc : kappa;
       if (nc > kappa) {
@@ -1001,7 +1002,8 @@ __global__ void __launch_bounds__(256, 2) k_greedy(GrParams p) {
         __syncwarp();
         nc = nq;
       }
-      for (int j = lane; j < nq; j += 32) w.xd[w.q[j]] = (float)w.xq[j];
+      if (ALGO == kBiht)
+        for (int j = lane; j < nq; j += 32) w.xd[w.q[j]] = (float)w.xq[j];
       __syncwarp();
 
       // ---- step 4: r = y - A x, Delta (FP64) ----
@@ -1088,10 +1090,20 @@ __global__ void __launch_bounds__(256, 2) k_greedy(GrParams p) {
       if (lane == 0) atomicOr(p.status, kStNotSpd);
     }
     // output and reset
-    for (int n = lane; n < N; n += 32) {
-      cb.X[pix * N + n] = w.xd[n];
-      w.xd[n] = 0.f;
-      w.inc[n] = 0;
+    if (ALGO == kBiht) {
+      for (int n = lane; n < N; n += 32) {
+        cb.X[pix * N + n] = w.xd[n];
+        w.xd[n] = 0.f;
+        w.inc[n] = 0;
+      }
+    } else {
+      // x = xq on the atoms q, zero elsewhere
+      for (int n = lane; n < N; n += 32) {
+        cb.X[pix * N + n] = 0.f;
+        w.inc[n] = 0;
+      }
+      __syncwarp();
+      for (int j = lane; j < nq; j += 32) cb.X[pix * N + w.q[j]] = (float)w.xq[j];
     }
     if (lane == 0) {
       if (cb.iters_out) cb.iters_out[pix] = it;
@@ -1175,6 +1187,13 @@ void capacities(GrParams& p, GreedyAlgo algo, const GreedyArgs& a, int Mmax, int
   p.cmax = cmax;
   p.dmax = cmax < Mmax ? cmax : Mmax;
   p.kmax = K > 0 ? K : 1;
+  int sel = p.kmax;
+  if (algo == kCosamp) sel = 2 * p.kmax;
+  if (algo == kGomp) {
+    const int gmax = a.G > 0 ? a.G : (K / 5 > 1 ? K / 5 : 1);
+    if (gmax > sel) sel = gmax;
+  }
+  p.selmax = sel;
 }
 
 void scalars(GrParams& p, GreedyAlgo algo, const GreedyArgs& a) {
@@ -1217,7 +1236,8 @@ cudaError_t run_greedy(Ctx& c, GreedyAlgo algo, const GreedyArgs& a, const GrCub
   capacities(p, algo, a, Mmax, Nmax);
   // FP32 factors in shared memory; the rare FP64 fallback (and the |c| > M minimum-norm
   // solve) use one global slot per resident warp, so more warps fit on an SM.
-  Layout lay(Mmax, Nmax, p.cmax, p.dmax, p.kmax, false, algo == kGomp, algo != kGomp);
+  Layout lay(Mmax, Nmax, p.cmax, p.dmax, p.kmax, p.selmax, false, algo == kGomp,
+             algo != kGomp, algo == kBiht);
   p.warp_bytes = lay.total;
   // one CTA of up to 8 warps per SM, or two smaller ones if that seats more warps
   int warps1 = (220 * 1024) / lay.total, warps2 = (110 * 1024) / lay.total;
@@ -1423,7 +1443,7 @@ cudaError_t launch_gomp_noalloc(const double* A64, int M, int N, const GreedyArg
   p.status = reinterpret_cast<int*>(s + lay.status);
   p.counter = reinterpret_cast<unsigned long long*>(s + lay.counter);
   capacities(p, kGomp, a, M, N);
-  Layout wl(M, N, p.cmax, p.dmax, p.kmax, true, true, false);
+  Layout wl(M, N, p.cmax, p.dmax, p.kmax, p.selmax, true, true, false, false);
   p.warp_bytes = wl.total;
   int warps = (220 * 1024) / wl.total;
   if (warps > 8) warps = 8;
