@@ -348,7 +348,9 @@ __device__ bool chol32(Warp& w, float* L, float* invd, int n, const int16_t* ato
         for (int r = 0; r < VR; ++r) tc[r] = t[r][c];
         const float d = __shfl_sync(0xffffffffu, rpick<VR>(tc, slot), src);
         if (!(d > 1e-4f * invd[col])) return false;  // warp-uniform
-        const float dj = sqrtf(d), inv = 1.f / dj;
+        // the FP32 factor only preconditions the FP64 refinement: the hardware reciprocal
+        // square root (a couple of ulps) serves for both the pivot and its inverse
+        const float inv = rsqrtf(d), dj = d * inv;
 #pragma unroll
         for (int r = 0; r < VR; ++r) {
           const int i = lane + 32 * r;
@@ -729,6 +731,12 @@ __device__ bool ls_min_norm(Warp& w, const int16_t* atoms, int n, double* s) {
   return true;
 }
 
+// sqrt(ss) in FP32, rounded up with a margin for the conversion of ss: an upper bound of
+// the FP64 norm, which is all the FP32 error bound of the correlation needs.
+__device__ __forceinline__ float norm_up(double ss) {
+  return __fsqrt_ru(__double2float_ru(ss)) * 1.000001f;
+}
+
 // SplitMix64's output mixing function (Steele, Lea and Flood, OOPSLA 2014).
 __device__ __forceinline__ unsigned long long mix64(unsigned long long z) {
   z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
@@ -788,7 +796,7 @@ __global__ void __launch_bounds__(256, 2) k_greedy(GrParams p) {
   }
   __syncwarp();
   int cur = -1;        // cube whose data w.cb holds
-  double cnorm = 0.0;  // its largest column norm
+  float cnorm = 0.f;  // its largest column norm, rounded up
 
   for (;;) {
     unsigned long long pix_u = 0;
@@ -813,7 +821,7 @@ __global__ void __launch_bounds__(256, 2) k_greedy(GrParams p) {
       // of the correlation
       double cn2 = 0.0;
       for (int n = lane; n < w.cb->N; n += 32) cn2 = fmax(cn2, w.cb->G64[(size_t)n * w.cb->N + n]);
-      cnorm = sqrt(warp_max(cn2));
+      cnorm = norm_up(warp_max(cn2));
     }
     const GrCube& cb = *w.cb;
     const int M = cb.M, N = cb.N;
@@ -838,7 +846,7 @@ __global__ void __launch_bounds__(256, 2) k_greedy(GrParams p) {
       r2 += (double)yv * yv;
     }
     if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(p.status, kStNonFinite);
-    double rnorm = sqrt(warp_sum(r2));  // ||r||_2, FP64
+    float rnorm = norm_up(warp_sum(r2));  // ||r||_2, rounded up (the certification bound)
     __syncwarp();
     if (!p.start_done && cap > 0) load_rhs(w);
 
@@ -886,7 +894,8 @@ __global__ void __launch_bounds__(256, 2) k_greedy(GrParams p) {
       {
         // FP32 error bound of the correlation: the sum of M products of rounded A and r
         // errs by at most (M + 2) u sum |A_mj r_m| <= (M + 2) u ||A_j|| ||r||, u = 2^-24
-        const double pbound = (M + 4) * 0x1p-24 * 1.01 * cnorm * rnorm;
+        // (FP32 arithmetic: the 1% margin covers its own roundings)
+        const float pbound = (M + 4) * 0x1p-24f * 1.01f * cnorm * rnorm;
         if (ALGO == kBiht) {
           // u = x + mu p adds the roundings of x, mu and of the update itself
           float um = 0.f, xm = 0.f;
@@ -900,9 +909,9 @@ __global__ void __launch_bounds__(256, 2) k_greedy(GrParams p) {
           }
           um = warp_max(um);
           xm = warp_max(xm);
-          const double E =
-              p.mu64 * pbound + 0x1p-24 * 1.01 * ((double)um + xm + p.mu64 * cnorm * rnorm);
-          certify_topk(w, val, N, ksel, tk, (float)(E * 1.001),
+          const float mu_up = fabsf(p.mu) * 1.000001f;  // |mu| rounded to FP32, and up
+          const float E = mu_up * pbound + 0x1p-24f * 1.01f * (um + xm + mu_up * cnorm * rnorm);
+          certify_topk(w, val, N, ksel, tk, E * 1.001f,
                        [&](int j) {
                          const double* a = cb.At64 + (size_t)j * M;
                          double g = 0.0;
@@ -914,7 +923,7 @@ __global__ void __launch_bounds__(256, 2) k_greedy(GrParams p) {
                        },
                        w.sel);
         } else {
-          certify_topk(w, val, N, ksel, tk, (float)(pbound * 1.001),
+          certify_topk(w, val, N, ksel, tk, pbound * 1.001f,
                        [&](int j) {
                          const double* a = cb.At64 + (size_t)j * M;
                          double g = 0.0;
@@ -1034,7 +1043,7 @@ __global__ void __launch_bounds__(256, 2) k_greedy(GrParams p) {
         }
       }
       d2 = warp_sum(d2);
-      rnorm = sqrt(warp_sum(rr));
+      rnorm = norm_up(warp_sum(rr));
       __syncwarp();
       work += 2.0 * M * nq;
       ++it;
