@@ -372,26 +372,39 @@ __device__ bool chol32(Warp& w, float* L, float* invd, int n, const int16_t* ato
 // lanes t < i read L(i, t)) on register-distributed vectors.
 template <int VR>
 __device__ void fwd32(const float* L, const float* invd, int n, float (&v)[VR], int lane) {
-  for (int i = 0; i < n; ++i) {
-    float vi = __shfl_sync(0xffffffffu, rpick<VR>(v, i >> 5), i & 31) * invd[i];
+  // rows of slot S (i in [32S, 32S + 32)) come from lane i - 32S's v[S]; slots below S
+  // hold rows < i and stay, slot S updates its rows past i, slots above S all their rows
 #pragma unroll
-    for (int k = 0; k < VR; ++k) {
-      int t = lane + 32 * k;
-      if (t == i) v[k] = vi;
-      else if (t > i && t < n) v[k] = fmaf(-L[ridx(t, i)], vi, v[k]);
+  for (int S = 0; S < VR; ++S) {
+    const int iend = min(n, 32 * S + 32);
+    for (int i = 32 * S; i < iend; ++i) {
+      const float vi = __shfl_sync(0xffffffffu, v[S], i - 32 * S) * invd[i];
+      const int t = lane + 32 * S;
+      if (t == i) v[S] = vi;
+      else if (t > i && t < n) v[S] = fmaf(-L[ridx(t, i)], vi, v[S]);
+#pragma unroll
+      for (int k = S + 1; k < VR; ++k) {
+        const int tk = lane + 32 * k;
+        if (tk < n) v[k] = fmaf(-L[ridx(tk, i)], vi, v[k]);
+      }
     }
   }
 }
 template <int VR>
 __device__ void bwd32(const float* L, const float* invd, int n, float (&v)[VR], int lane) {
-  for (int i = n - 1; i >= 0; --i) {
-    float si = __shfl_sync(0xffffffffu, rpick<VR>(v, i >> 5), i & 31) * invd[i];
-    const float* row = L + ridx(i, 0);
+  // rows from the last down: slot S's rows update the rows below them in slot S and all
+  // rows of the slots below S
 #pragma unroll
-    for (int k = 0; k < VR; ++k) {
-      int t = lane + 32 * k;
-      if (t == i) v[k] = si;
-      else if (t < i) v[k] = fmaf(-row[t], si, v[k]);
+  for (int S = VR - 1; S >= 0; --S) {
+    const int iend = min(n, 32 * S + 32);
+    for (int i = iend - 1; i >= 32 * S; --i) {
+      const float si = __shfl_sync(0xffffffffu, v[S], i - 32 * S) * invd[i];
+      const float* row = L + ridx(i, 0);
+      const int t = lane + 32 * S;
+      if (t == i) v[S] = si;
+      else if (t < i) v[S] = fmaf(-row[t], si, v[S]);
+#pragma unroll
+      for (int k = 0; k < S; ++k) v[k] = fmaf(-row[lane + 32 * k], si, v[k]);
     }
   }
 }
@@ -411,7 +424,7 @@ __device__ bool refine32(Warp& w, const float* L, const float* invd, int n,
     sr[k] = 0.0;
     rr[k] = t < n ? b[t] : 0.0;
   }
-  float prev = 3.0e38f;
+  float prev = 3.0e38f, smax = 0.f;  // smax: max |s| of the first solve, the test's scale
   for (int step = 0; step < 5; ++step) {
     float f[VR];
 #pragma unroll
@@ -419,21 +432,19 @@ __device__ bool refine32(Warp& w, const float* L, const float* invd, int n,
     fwd32<VR>(L, invd, n, f, lane);
     bwd32<VR>(L, invd, n, f, lane);
     float dm = 0.f;
-    double sm = 0.0;
 #pragma unroll
     for (int k = 0; k < VR; ++k) {
       int t = lane + 32 * k;
       if (t < n) {
         sr[k] += (double)f[k];
         dm = fmaxf(dm, fabsf(f[k]));
-        sm = fmax(sm, fabs(sr[k]));
         s[t] = sr[k];
       }
     }
     dm = warp_max(dm);
-    sm = warp_max(sm);
+    if (step == 0) smax = dm;  // the first correction is the FP32 solution itself
     __syncwarp();
-    if ((double)dm <= 1e-9 * sm) return true;
+    if (dm <= 1e-9f * smax) return true;
     if (step > 0 && dm > 0.5f * prev) return false;
     prev = dm;
     // r = b - G_c s in FP64; by symmetry lane t reads G(c_j, c_t) from row c_j, so a
