@@ -145,15 +145,23 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_admm_tc(AtcParams p) {
 
   if (__syncthreads_or(!done)) {
     for (int i = 1;; ++i) {
-      // ---- D = z - w, the operand of GEMM1
+      // ---- D = z - w, the operand of GEMM1 (two 8-column chunks per TMEM round trip)
 #pragma unroll
-      for (int c = 0; c < NH; c += 8) {
-        float zc[8], d[8];
-        tc::tmem_ld8(tZ + n0 + c, zc);
+      for (int c2 = 0; c2 < NH; c2 += 16) {
+        float zc[2][8];
+        tc::tmem_ld8(tZ + n0 + c2, zc[0]);
+        if (c2 + 8 < NH) tc::tmem_ld8(tZ + n0 + c2 + 8, zc[1]);
         tc::tmem_wait_ld();
 #pragma unroll
-        for (int e = 0; e < 8; ++e) d[e] = zc[e] - w[c + e];
-        tc::put_operand8(sO, Np, r, n0 + c, d);
+        for (int h = 0; h < 2; ++h) {
+          const int c = c2 + 8 * h;
+          if (c < NH) {
+            float d[8];
+#pragma unroll
+            for (int e = 0; e < 8; ++e) d[e] = zc[h][e] - w[c + e];
+            tc::put_operand8(sO, Np, r, n0 + c, d);
+          }
+        }
       }
       if (!tile_product(&mbar, phase, tR, uO, uAh, uAl, Np, S, false, id1)) {
         failed = true;
@@ -161,14 +169,25 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_admm_tc(AtcParams p) {
       }
       // ---- E = Y - T, the operand of GEMMW
 #pragma unroll
-      for (int c = 0; c < MH; c += 8) {
-        float t[8], y8[8], e8[8];
-        tc::tmem_ld8(tR + m0 + c, t);
-        tc::tmem_ld8(tY + c, y8);
+      for (int c2 = 0; c2 < MH; c2 += 16) {
+        float t[2][8], y8[2][8];
+        tc::tmem_ld8(tR + m0 + c2, t[0]);
+        tc::tmem_ld8(tY + c2, y8[0]);
+        if (c2 + 8 < MH) {
+          tc::tmem_ld8(tR + m0 + c2 + 8, t[1]);
+          tc::tmem_ld8(tY + c2 + 8, y8[1]);
+        }
         tc::tmem_wait_ld();
 #pragma unroll
-        for (int e = 0; e < 8; ++e) e8[e] = y8[e] - t[e];
-        tc::put_operand8(sO, Mp, r, m0 + c, e8);
+        for (int h = 0; h < 2; ++h) {
+          const int c = c2 + 8 * h;
+          if (c < MH) {
+            float e8[8];
+#pragma unroll
+            for (int e = 0; e < 8; ++e) e8[e] = y8[h][e] - t[h][e];
+            tc::put_operand8(sO, Mp, r, m0 + c, e8);
+          }
+        }
       }
       if (!tile_product(&mbar, phase, tR, uO, uWh, uWl, Mp, SW, true, idw)) {
         failed = true;
@@ -177,17 +196,24 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_admm_tc(AtcParams p) {
       // ---- h: Delta_i = rho ||h - h_prev||, and H, the operand of GEMM2
       float d2 = 0.f;
 #pragma unroll
-      for (int c = 0; c < MH; c += 8) {
-        float h[8];
-        tc::tmem_ld8(tR + m0 + c, h);
+      for (int c2 = 0; c2 < MH; c2 += 16) {
+        float hh[2][8];
+        tc::tmem_ld8(tR + m0 + c2, hh[0]);
+        if (c2 + 8 < MH) tc::tmem_ld8(tR + m0 + c2 + 8, hh[1]);
         tc::tmem_wait_ld();
 #pragma unroll
-        for (int e = 0; e < 8; ++e) {
-          float df = h[e] - hp[c + e];
-          d2 += df * df;
-          hp[c + e] = h[e];
+        for (int q = 0; q < 2; ++q) {
+          const int c = c2 + 8 * q;
+          if (c < MH) {
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+              float df = hh[q][e] - hp[c + e];
+              d2 += df * df;
+              hp[c + e] = hh[q][e];
+            }
+            tc::put_operand8(sO, Mp, r, m0 + c, hh[q]);
+          }
         }
-        tc::put_operand8(sO, Mp, r, m0 + c, h);
       }
       red[half * 128 + r] = d2;
       if (!tile_product(&mbar, phase, tR, uO, uAh, uAl, Mp, S, true, id2)) {
@@ -199,26 +225,37 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_admm_tc(AtcParams p) {
       const bool fin = !done && (conv_now || i == p.iters);
       // ---- x = d + A^T h, z = soft(x + w, lambda / rho), w = w + x - z
 #pragma unroll
-      for (int c = 0; c < NH; c += 8) {
-        float C[8], zc[8], xo[8];
-        tc::tmem_ld8(tR + n0 + c, C);
-        tc::tmem_ld8(tZ + n0 + c, zc);
+      for (int c2 = 0; c2 < NH; c2 += 16) {
+        float C[2][8], zc[2][8];
+        tc::tmem_ld8(tR + n0 + c2, C[0]);
+        tc::tmem_ld8(tZ + n0 + c2, zc[0]);
+        if (c2 + 8 < NH) {
+          tc::tmem_ld8(tR + n0 + c2 + 8, C[1]);
+          tc::tmem_ld8(tZ + n0 + c2 + 8, zc[1]);
+        }
         tc::tmem_wait_ld();
 #pragma unroll
-        for (int e = 0; e < 8; ++e) {
-          const float x = (zc[e] - w[c + e]) + C[e];
-          xo[e] = x;
-          if (!done) {
-            const float zn = tc::soft_thr(x + w[c + e], p.thr);
-            w[c + e] = w[c + e] + x - zn;
-            zc[e] = zn;
-          }
-        }
-        tc::tmem_st8(tZ + n0 + c, zc);
-        if (fin) {
+        for (int q = 0; q < 2; ++q) {
+          const int c = c2 + 8 * q;
+          if (c < NH) {
+            float xo[8];
 #pragma unroll
-          for (int e = 0; e < 8; ++e)
-            if (n0 + c + e < N) p.X[pix * N + n0 + c + e] = xo[e];
+            for (int e = 0; e < 8; ++e) {
+              const float x = (zc[q][e] - w[c + e]) + C[q][e];
+              xo[e] = x;
+              if (!done) {
+                const float zn = tc::soft_thr(x + w[c + e], p.thr);
+                w[c + e] = w[c + e] + x - zn;
+                zc[q][e] = zn;
+              }
+            }
+            tc::tmem_st8(tZ + n0 + c, zc[q]);
+            if (fin) {
+#pragma unroll
+              for (int e = 0; e < 8; ++e)
+                if (n0 + c + e < N) p.X[pix * N + n0 + c + e] = xo[e];
+            }
+          }
         }
       }
       tc::tmem_wait_st();

@@ -107,23 +107,31 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_fista_tc(FtcParams p) {
     //      Delta_{i-1} = ||u^{i-1} - u^{i-2}||  (u^0 = 0)
     float d2 = 0.f;
 #pragma unroll
-    for (int c = 0; c < MH; c += 8) {
-      float u[8], v[8];
+    for (int c2 = 0; c2 < MH; c2 += 16) {  // two 8-column chunks per TMEM round trip
+      float u[2][8];
       if (i > 1) {
-        tc::tmem_ld8(tR + m0 + c, u);
+        tc::tmem_ld8(tR + m0 + c2, u[0]);
+        if (c2 + 8 < MH) tc::tmem_ld8(tR + m0 + c2 + 8, u[1]);
         tc::tmem_wait_ld();
       } else {
 #pragma unroll
-        for (int e = 0; e < 8; ++e) u[e] = 0.f;
+        for (int e = 0; e < 8; ++e) u[0][e] = u[1][e] = 0.f;
       }
 #pragma unroll
-      for (int e = 0; e < 8; ++e) {
-        float df = u[e] - up[c + e];
-        d2 += df * df;
-        v[e] = u[e] + beta_prev * df - yv[c + e];
-        up[c + e] = u[e];
+      for (int h = 0; h < 2; ++h) {
+        const int c = c2 + 8 * h;
+        if (c < MH) {
+          float v[8];
+#pragma unroll
+          for (int e = 0; e < 8; ++e) {
+            float df = u[h][e] - up[c + e];
+            d2 += df * df;
+            v[e] = u[h][e] + beta_prev * df - yv[c + e];
+            up[c + e] = u[h][e];
+          }
+          put_operand8(sO, Mp, r, m0 + c, v);
+        }
       }
-      put_operand8(sO, Mp, r, m0 + c, v);
     }
     red[half * 128 + r] = d2;
     __syncthreads();
@@ -170,24 +178,36 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_fista_tc(FtcParams p) {
 
     // ---- steps 1-4: aux = z - C / L, x = soft(aux, lambda / L), t, z
     const float beta = p.beta[i - 1];
+    // two 8-column chunks per TMEM round trip
 #pragma unroll
-    for (int c = 0; c < NH; c += 8) {
-      float C[8], xp[8], xn[8];
-      tc::tmem_ld8(tR + n0 + c, C);
-      tc::tmem_ld8(tX + n0 + c, xp);
+    for (int c2 = 0; c2 < NH; c2 += 16) {
+      float C[2][8], xp[2][8];
+      tc::tmem_ld8(tR + n0 + c2, C[0]);
+      tc::tmem_ld8(tX + n0 + c2, xp[0]);
+      if (c2 + 8 < NH) {
+        tc::tmem_ld8(tR + n0 + c2 + 8, C[1]);
+        tc::tmem_ld8(tX + n0 + c2 + 8, xp[1]);
+      }
       tc::tmem_wait_ld();
 #pragma unroll
-      for (int e = 0; e < 8; ++e) {
-        float xx = soft_thr(z[c + e] - C[e] * p.invL, p.thr);
-        if (!done) {
-          z[c + e] = xx + beta * (xx - xp[e]);
-        } else {
-          xx = xp[e];
+      for (int h = 0; h < 2; ++h) {
+        const int c = c2 + 8 * h;
+        if (c < NH) {
+          float xn[8];
+#pragma unroll
+          for (int e = 0; e < 8; ++e) {
+            float xx = soft_thr(z[c + e] - C[h][e] * p.invL, p.thr);
+            if (!done) {
+              z[c + e] = xx + beta * (xx - xp[h][e]);
+            } else {
+              xx = xp[h][e];
+            }
+            xn[e] = xx;
+          }
+          tc::tmem_st8(tX + n0 + c, xn);
+          put_operand8(sO, Np, r, n0 + c, xn);
         }
-        xn[e] = xx;
       }
-      tc::tmem_st8(tX + n0 + c, xn);
-      put_operand8(sO, Np, r, n0 + c, xn);
     }
     tc::tmem_wait_st();
 

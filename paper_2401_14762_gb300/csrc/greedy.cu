@@ -268,7 +268,7 @@ __device__ bool chol32(Warp& w, float* L, float* invd, int n, const int16_t* ato
   const int lane = w.lane, N = w.cb->N;
   // gather: G row atoms[k] (read at the sorted atoms, a few sectors) into column k;
   // several columns of loads are in flight before their stores
-  constexpr int kB = VR <= 2 ? 8 : 4;
+  constexpr int kB = 4;
   const float* G32 = w.cb->G32;
   const double* G64 = w.cb->G64;
   for (int k0 = 0; k0 < n; k0 += kB) {
