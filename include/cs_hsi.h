@@ -151,11 +151,12 @@ cs_status cs_recover_cosamp(cs_ctx *ctx, const float *Y, float *X, int64_t P, in
                             const cs_opts *opts);
 
 /* Algorithmic work of the last greedy call on this context (cs_recover_gomp, _biht,
- * _cosamp), in flops of the method as the paper states it: per pixel and iteration the
- * correlation A^T r (2MN), a Cholesky least-squares solve on the support of n atoms
- * (n^3/3 + 2n^2; the minimum-norm form n M^2 + M^3/3 + 2M^2 + nM when n > M), gOMP's
- * refit on its kappa atoms, and the residual y - A x (2M|supp x|).  Implementation extras
- * (refinement passes, padding) are not counted.  Waits for the context's stream. */
+ * _cosamp), in flops: per pixel and iteration the correlation A^T r (2MN), a Cholesky
+ * least-squares solve on the support of n atoms (n^3/3 + 2n^2; the minimum-norm form
+ * n M^2 + M^3/3 + 2M^2 + nM when n > M; for gOMP, whose factor grows with its support,
+ * the rows appended, i^2 flops for row i, + 2n^2), gOMP's refit on its kappa atoms when it
+ * is performed, and the residual y - A x (2M|supp x|).  Implementation extras (refinement
+ * passes, padding) are not counted.  Waits for the context's stream. */
 cs_status cs_get_work(cs_ctx *ctx, double *flops);
 
 /* gOMP exactly as cs_recover_gomp, for callers that cannot allocate device memory when

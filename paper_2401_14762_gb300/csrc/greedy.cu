@@ -10,9 +10,11 @@
 //      large k; the choice is then certified against FP64: atoms whose FP32 value lies
 //      within the FP32 error bound of the cut are recomputed in FP64 and ranked exactly,
 //      so every selection is the one FP64 arithmetic makes,
-//   3. forms the support c (union of Theta with c or supp(x)), kept sorted by atom,
+//   3. forms the support c (union of Theta with c or supp(x)): sorted by atom for BIHT
+//      and CoSaMP, in order of arrival for gOMP, whose support only grows,
 //   4. solves min ||A_c s - y|| through the normal equations G_c s = (A^T y)_c: G_c is
-//      gathered from the precomputed FP64 Gram matrix A^T A, factored in FP32, and the
+//      gathered from the precomputed Gram matrix A^T A, factored in FP32 (gOMP extends
+//      its factor by the rows of the atoms just added instead of refactoring), and the
 //      solution is refined to FP64 accuracy with FP64 residuals (an FP64 factorisation
 //      is the fallback); when |c| > M the minimum-norm solution s = A_c^T (A_c A_c^T)^{-1} y
 //      is used instead,
@@ -482,6 +484,49 @@ __device__ bool refine32(Warp& w, const float* L, const float* invd, int n,
   return false;
 }
 
+// Extends the FP32 factor of G_c from its first nf rows to n rows, for atoms appended at
+// the end of c (gOMP's growing support): row i is w = L_{0:i}^{-1} G(c_{0:i}, c_i), one
+// forward sweep with the factor built so far, and L(i, i) = sqrt(G(c_i, c_i) - ||w||^2).
+// Returns false when a pivot drops below 1e-4 of its diagonal.
+template <int VR>
+__device__ bool chol32_append(Warp& w, float* L, float* invd, int nf, int n,
+                              const int16_t* atoms) {
+  const int lane = w.lane, N = w.cb->N;
+  const float* G32 = w.cb->G32;
+  const double* G64 = w.cb->G64;
+  for (int i = nf; i < n; ++i) {
+    const size_t row = (size_t)atoms[i] * N;
+    float g[VR];
+#pragma unroll
+    for (int k = 0; k < VR; ++k) {
+      const int t = lane + 32 * k;
+      const int col = atoms[min(t, i)];
+      const float v = G32 ? __ldg(G32 + row + col) : (float)__ldg(G64 + row + col);
+      g[k] = t < i ? v : 0.f;
+    }
+    const float gii = G32 ? __ldg(G32 + row + atoms[i]) : (float)__ldg(G64 + row + atoms[i]);
+    fwd32<VR>(L, invd, i, g, lane);  // g := L_{0:i}^{-1} g
+    float ss = 0.f;
+#pragma unroll
+    for (int k = 0; k < VR; ++k) {
+      const int t = lane + 32 * k;
+      if (t < i) {
+        ss = fmaf(g[k], g[k], ss);
+        L[ridx(i, t)] = g[k];
+      }
+    }
+    const float d = gii - warp_sum(ss);
+    if (!(d > 1e-4f * gii)) return false;  // warp-uniform
+    const float inv = rsqrtf(d);
+    if (lane == 0) {
+      L[ridx(i, i)] = d * inv;
+      invd[i] = inv;
+    }
+    __syncwarp();
+  }
+  return true;
+}
+
 // Least squares on atoms[0..n) (n <= M): mixed precision first, FP64 factorisation if
 // the FP32 factor fails.  b goes to vbuf; Lbuf/invdbuf hold FP32 or FP64 factors.
 template <int VR>
@@ -705,6 +750,27 @@ __device__ bool ls_solve(Warp& w, const int16_t* atoms, int n, double* Lbuf, dou
   return ls_fresh(w, atoms, n, Lbuf, invdbuf, vbuf, s, cap);
 }
 
+// Least squares on a support that only grows (gOMP): the FP32 factor of its first nf
+// atoms carries over from the last call and is extended to n rows; nf is updated to the
+// rows it holds afterwards (0 when the factor must be rebuilt).
+template <int VR>
+__device__ bool ls_solve_grow(Warp& w, const int16_t* atoms, int& nf, int n, double* Lbuf,
+                              double* invdbuf, double* vbuf, double* s, int cap) {
+  fill_rhs(w, atoms, n, vbuf);
+  float* L32 = reinterpret_cast<float*>(Lbuf);
+  float* inv32 = reinterpret_cast<float*>(invdbuf);
+  const bool factored = chol32_append<VR>(w, L32, inv32, nf, n, atoms);
+  nf = factored ? n : 0;
+  if (factored && refine32<VR>(w, L32, inv32, n, atoms, vbuf, s)) return true;
+  if (w.fb) {
+    const int D = w.p.dmax;
+    double* Lg = w.fb;
+    return ls_fresh(w, atoms, n, Lg, Lg + D * (D + 1) / 2, Lg + D * (D + 1) / 2 + D, s, D);
+  }
+  nf = 0;  // the FP64 fallback below overwrites the FP32 factor's region
+  return ls_fresh(w, atoms, n, Lbuf, invdbuf, vbuf, s, cap);
+}
+
 // Minimum-norm solution for |c| > M: s = A_c^T H^{-1} y with H = A_c A_c^T (M x M).
 __device__ bool ls_min_norm(Warp& w, const int16_t* atoms, int n, double* s) {
   const int M = w.cb->M;
@@ -862,6 +928,7 @@ __global__ void __launch_bounds__(256, 2) k_greedy(GrParams p) {
     if (!p.start_done && cap > 0) load_rhs(w);
 
     int nc = 0, nq = 0, it = 0;
+    int nf = 0;  // gOMP: rows of the FP32 factor of G_c carried over between iterations
     uint8_t conv = 0;
     // cycle search over the iterates x_it (BIHT, CoSaMP): ring[it % 32] holds a hash of
     // x_it; a hash seen `period` iterations ago nominates a cycle, which is confirmed by
@@ -945,17 +1012,33 @@ __global__ void __launch_bounds__(256, 2) k_greedy(GrParams p) {
         }
       }
 
-      // ---- support c = Theta U c (gOMP: the growing support; CoSaMP: the last pruned
-      // support; BIHT: supp(x)), marked in inc[] and listed in ascending atom order ----
+      // ---- support c = Theta U c (gOMP: the growing support, new atoms appended in
+      // selection order so its factor can be extended; CoSaMP: the last pruned support;
+      // BIHT: supp(x)), marked in inc[]; CoSaMP's and BIHT's c in ascending atom order ----
+      if (ALGO == kGomp) {
+        const unsigned below = (1u << lane) - 1u;
+        for (int b0 = 0; b0 < ksel; b0 += 32) {
+          const int j = b0 + lane;
+          const int a = j < ksel ? w.sel[j] : 0;
+          const bool isnew = j < ksel && !w.inc[a];
+          const unsigned m = __ballot_sync(0xffffffffu, isnew);
+          if (isnew) {
+            w.c[nc + __popc(m & below)] = (int16_t)a;
+            w.inc[a] = 1;
+          }
+          nc += __popc(m);
+          __syncwarp();
+        }
+      }
       if (ALGO == kBiht) {
         for (int n = lane; n < N; n += 32) w.inc[n] = 0;
         __syncwarp();
         for (int j = lane; j < nq; j += 32)
           if (w.xq[j] != 0.0) w.inc[w.q[j]] = 1;
       }
-      for (int j = lane; j < ksel; j += 32) w.inc[w.sel[j]] = 1;
-      __syncwarp();
-      {
+      if (ALGO != kGomp) {
+        for (int j = lane; j < ksel; j += 32) w.inc[w.sel[j]] = 1;
+        __syncwarp();
         const unsigned below = (1u << lane) - 1u;
         int cnt = 0;
         for (int a0 = 0; a0 < N; a0 += 32) {
@@ -970,8 +1053,11 @@ __global__ void __launch_bounds__(256, 2) k_greedy(GrParams p) {
       }
 
       // ---- step 2: least squares on c ----
+      const int nf0 = nf;
       if (nc > 0) {
-        if (nc <= M)
+        if (ALGO == kGomp)
+          fail |= !ls_solve_grow<VR>(w, w.c, nf, nc, w.L, w.invd, w.v, w.s, p.dmax);
+        else if (nc <= M)
           fail |= !ls_solve<VR>(w, w.c, nc, w.L, w.invd, w.v, w.s, p.dmax);
         else
           fail |= !ls_min_norm(w, w.c, nc, w.s);
@@ -979,8 +1065,16 @@ __global__ void __launch_bounds__(256, 2) k_greedy(GrParams p) {
       if (fail) break;
       {
         const double n = nc, m = M;
-        work += 2.0 * m * N +
-                (nc <= M ? n * n * n / 3.0 + 2.0 * n * n : n * m * m + m * m * m / 3.0 + 2.0 * m * m + n * m);
+        double ls;
+        if (ALGO == kGomp) {
+          // rows appended to the factor: a forward sweep of i^2 flops for row i
+          const double a = nf0, b = nc;  // rows [a, b)
+          ls = ((b - 1) * b * (2 * b - 1) - (a - 1) * a * (2 * a - 1)) / 6.0 + 2.0 * n * n;
+        } else {
+          ls = nc <= M ? n * n * n / 3.0 + 2.0 * n * n
+                       : n * m * m + m * m * m / 3.0 + 2.0 * m * m + n * m;
+        }
+        work += 2.0 * m * N + ls;
       }
 
       // ---- step 3: prune to kappa (and refit for gOMP) ----
@@ -990,7 +1084,7 @@ __global__ void __launch_bounds__(256, 2) k_greedy(GrParams p) {
       __syncwarp();
       int keep = nc < kappa ? nc : kappa;
       if (nc > kappa) {
-        topk_select_positions(w, w.s, nc, keep, w.sel);  // c sorted: positions order atoms
+        topk_select_positions(w, w.s, nc, keep, w.sel);  // ascending positions of c
       } else {
         for (int j = lane; j < nc; j += 32) w.sel[j] = (int16_t)j;
         __syncwarp();
@@ -1001,7 +1095,7 @@ __global__ void __launch_bounds__(256, 2) k_greedy(GrParams p) {
         w.xq[j] = w.s[pos];
       }
       __syncwarp();
-      nq = keep;  // q inherits c's ascending order
+      nq = keep;  // q keeps the order of c
       // the refit on q; when q is all of c (in c's order) it would repeat the solve just
       // made, bit for bit, so x keeps that solution
       if (ALGO == kGomp && nq > 0 && nq < nc) {
