@@ -102,7 +102,7 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    n_pix = 256
+    n_pix = 2048
     cores = host_cores()
     Phi, X, E = sample_inputs(n_pix)
     for _ in range(args.warmup):
@@ -394,7 +394,7 @@ def run_gpu(args):
             kernels[k] = ent
 
         # accuracy against the oracle on a sample, and the CPU baseline
-        n_s = 512
+        n_s = 6144  # about 10 s of oracle time on 16 host cores
         cores = host_cores()
         Phi_s, Xs, Es = Phi, Xt[:n_s].double().cpu().numpy(), E[:n_s].double().cpu().numpy()
         ref, secs = oracle_sample(n_s, cores, Xs, Es, Phi_s)

@@ -136,3 +136,25 @@ def test_batch_argument_errors(cs):
     assert e.value.status == cs.CS_ERR_ARG
     with pytest.raises(cs.CsError):
         cs.cs_recover_batch([], cs.CS_ALGO_GOMP, kappa=8, G=2)
+
+
+def test_batch_many_small_cubes(cs):
+    """More cubes than one descriptor upload carries (32), several of one dictionary:
+    every cube equals its single-cube call bit for bit."""
+    torch = torch_cuda()
+    ctxs = [cs.cs_create(48, 120, Phi=sy.gaussian_phi(48, 120, 70 + i % 5)) for i in range(5)]
+    probs, items = [], []
+    for i in range(41):
+        pr = Problem(48, 120, 3 + (7 * i) % 19, "sparse", seed=70 + i % 5, S=5,
+                     amplitude="separated")
+        ctx = ctxs[i % 5]
+        X = torch.full((pr.P, 120), float("nan"), device="cuda")
+        it = torch.full((pr.P,), -1, device="cuda", dtype=torch.int32)
+        items.append({"ctx": ctx, "Y": torch.from_numpy(pr.Y).cuda(), "X": X, "iters_out": it})
+        probs.append((pr, ctx, X, it))
+    cs.cs_recover_batch(items, cs.CS_ALGO_COSAMP, kappa=6, opts=cs.make_opts())
+    cs.cs_sync(ctxs[0])
+    for pr, ctx, X, it in probs:
+        Xs, its, _ = gpu_run(cs.cs_recover_cosamp, ctx, pr.Y, 120, 6)
+        assert np.array_equal(X.cpu().numpy().view(np.uint32), Xs.view(np.uint32))
+        assert np.array_equal(it.cpu().numpy(), its)

@@ -52,3 +52,10 @@ def test_errors_before_any_device_work(lib):
     assert lib.cs_sync(None) == cs.CS_ERR_ARG
     assert "ctx" in cs.cs_last_error()
     lib.cs_destroy(None)
+    # batches: empty, NULL parameters or an unknown algorithm are argument errors
+    prm = cs.cs_algo_params(1e-3, 1.0, 10, 4, 2)
+    items = (cs.cs_batch_item * 1)()
+    assert lib.cs_recover_batch(None, 1, cs.CS_ALGO_GOMP, ctypes.byref(prm), None) == cs.CS_ERR_ARG
+    assert lib.cs_recover_batch(items, 0, cs.CS_ALGO_GOMP, ctypes.byref(prm), None) == cs.CS_ERR_ARG
+    assert lib.cs_recover_batch(items, 1, cs.CS_ALGO_GOMP, None, None) == cs.CS_ERR_ARG
+    assert lib.cs_recover_batch(items, 1, 7, ctypes.byref(prm), None) == cs.CS_ERR_ARG
