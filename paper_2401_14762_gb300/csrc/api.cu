@@ -47,6 +47,7 @@ void free_ctx(Ctx& c) {
   cudaFree(c.At32);
   cudaFree(c.W32);
   cudaFree(c.W64);
+  cudaFree(c.Wpad);
   cudaFree(c.cube_table);
   cudaFree(c.scratch64);
   cudaFree(c.status);
@@ -175,6 +176,7 @@ cs_status cs_create(cs_ctx** out, int M, int N, const double* A_host, const doub
       (e = cs::dalloc(&c.At32, (size_t)N * M)) != cudaSuccess ||
       (e = cs::dalloc(&c.W32, (size_t)M * M)) != cudaSuccess ||
       (e = cs::dalloc(&c.W64, (size_t)M * M)) != cudaSuccess ||
+      (e = cs::dalloc(&c.Wpad, (size_t)M * cs::smem_ld(M))) != cudaSuccess ||
       (e = cs::dalloc(&c.scratch64, c.scratch_elems)) != cudaSuccess ||
       (e = cs::dalloc(&c.status, 1)) != cudaSuccess ||
       (e = cs::dalloc(&c.counter, 2)) != cudaSuccess ||

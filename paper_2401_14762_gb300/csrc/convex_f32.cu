@@ -32,6 +32,8 @@ struct CvParams {
   int M, N, Npad, lda, ldw, Mpad;
   const float* A;  // M x N global
   const float* W;  // M x M global (ADMM)
+  const float* Wg; // the same with rows padded to ldw, read from global memory when the
+                   // kernel's shared-memory layout has no room for W (else null)
   const float* Y;
   float* X;
   const float* E;  // measurement noise (measure only)
@@ -261,9 +263,11 @@ template <int MR, int NCH>
 __global__ void __launch_bounds__(kThreads, 1) k_admm_f32(CvParams p) {
   extern __shared__ __align__(16) float sm[];
   const int M = p.M, lda = p.lda, ldw = p.ldw;
+  const bool w_smem = p.Wg == nullptr;
   float* As = sm;
   float* Ws = As + M * lda;
-  float* xs = Ws + M * ldw;
+  float* xs = w_smem ? Ws + M * ldw : Ws;
+  const float* Wr = w_smem ? Ws : p.Wg;
   float* es = xs + kT * lda;
   float* vs = es + kT * ldw;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -271,7 +275,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_admm_f32(CvParams p) {
   const float rho = p.c1, thr = p.c2;
 
   stage_matrix(As, p.A, M, p.N, lda);
-  stage_matrix(Ws, p.W, M, M, ldw);
+  if (w_smem) stage_matrix(Ws, p.W, M, M, ldw);
   for (int i = tid; i < kT * lda; i += kThreads) xs[i] = 0.f;
   for (int i = tid; i < kT * ldw; i += kThreads) es[i] = 0.f;
 
@@ -332,7 +336,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_admm_f32(CvParams p) {
     __syncwarp();
     // h = W e ; r = rho h ; Delta = rho ||h - h_prev||
     float h[kPPW][MR];
-    rows_product<MR>(h, Ws, ldw, es, ldw, p.Mpad, warp, row, hr);
+    rows_product<MR>(h, Wr, ldw, es, ldw, p.Mpad, warp, row, hr);
     ++it;
     bool fin[kPPW], conv[kPPW];
 #pragma unroll
@@ -479,8 +483,13 @@ cudaError_t fista_mr(const Ctx& c, CvParams p, int64_t blocks) {
 
 template <int MR, int NCH>
 cudaError_t admm_mr(const Ctx& c, CvParams p, int64_t blocks) {
-  size_t smem = sizeof(float) * ((size_t)c.M * p.lda + (size_t)c.M * p.ldw + (size_t)kT * p.lda +
-                                 (size_t)kT * p.ldw + (size_t)c.M * kLdv);
+  const size_t tiles = (size_t)kT * p.lda + (size_t)kT * p.ldw + (size_t)c.M * kLdv;
+  size_t smem = sizeof(float) * ((size_t)c.M * p.lda + (size_t)c.M * p.ldw + tiles);
+  if (smem > 227 * 1024) {
+    // no room for W: its padded copy is read through L1/L2 instead (M x M, <= 66 KB)
+    p.Wg = c.Wpad;
+    smem = sizeof(float) * ((size_t)c.M * p.lda + tiles);
+  }
   allow_smem(k_admm_f32<MR, NCH>, smem);
   k_admm_f32<MR, NCH><<<(unsigned)blocks, kThreads, smem, c.stream>>>(p);
   return cudaGetLastError();

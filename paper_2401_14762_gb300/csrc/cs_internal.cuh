@@ -42,6 +42,7 @@ struct Ctx {
   double rho = 0.0;           // penalty of the cached ADMM factor
   float* W32 = nullptr;       // M x M, FP32 (A A^T + rho I)^{-1}
   double* W64 = nullptr;      // M x M, the same in FP64 (split for the tensor cores)
+  float* Wpad = nullptr;      // M x smem_ld(M), the FP32 factor with zero-padded rows
   double* scratch64 = nullptr;  // setup scratch
   size_t scratch_elems = 0;
   int* status = nullptr;      // device status word

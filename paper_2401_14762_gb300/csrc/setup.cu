@@ -198,6 +198,15 @@ __global__ void __launch_bounds__(1024) k_spd_inverse(int n, const double* K, do
   }
 }
 
+// dst (rows x ld) = src (rows x cols) with each row zero padded to ld columns.
+__global__ void k_pad_rows(int rows, int cols, int ld, const float* src, float* dst) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < rows * ld) {
+    int r = i / ld, c = i - r * ld;
+    dst[i] = c < cols ? src[r * cols + c] : 0.f;
+  }
+}
+
 __global__ void k_add_diag(int n, double* K, double v) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) K[i * n + i] += v;
@@ -254,6 +263,8 @@ cudaError_t setup_admm_factor(Ctx& c, double rho) {
   k_gemm_f64<<<nblk(M * M, 256), 256, 0, s>>>(M, M, N, c.A64, N, 1, c.A64, 1, N, K);
   k_add_diag<<<nblk(M, 256), 256, 0, s>>>(M, K, rho);
   k_spd_inverse<<<1, 1024, 0, s>>>(M, K, work, c.W32, c.W64, c.status);
+  const int ldw = smem_ld(M);
+  k_pad_rows<<<nblk(M * ldw, 256), 256, 0, s>>>(M, M, ldw, c.W32, c.Wpad);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   c.rho = rho;

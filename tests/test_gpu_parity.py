@@ -331,3 +331,31 @@ def test_argument_errors(cs, small):
         with pytest.raises(cs.CsError) as e:
             f()
         assert e.value.status == cs.CS_ERR_ARG
+
+
+# --------------------------------------------------------------------------- maximum sizes
+@pytest.mark.parametrize("algo,kappa,G", [("gomp", 16, 8), ("biht", 60, 0), ("cosamp", 42, 0)])
+def test_greedy_maximum_shape(cs, algo, kappa, G):
+    """M = 128, N = 256 (the largest dictionary) with supports of up to 120-128 atoms, the
+    widest register layout of the greedy kernel: exact against the oracle."""
+    pr = Problem(128, 256, 70, "sparse", seed=31, S=12, amplitude="separated")
+    ctx = cs.cs_create(128, 256, Phi=pr.Phi)
+    if algo == "gomp":
+        Xo, ito, _ = orc.gomp(pr.A, pr.Y, kappa, G)
+        Xg, it, _ = gpu_run(cs.cs_recover_gomp, ctx, pr.Y, 256, kappa, G)
+    elif algo == "biht":
+        Xo, ito, _ = orc.biht(pr.A, pr.Y, kappa, 1.0)
+        Xg, it, _ = gpu_run(cs.cs_recover_biht, ctx, pr.Y, 256, kappa, mu=1.0)
+    else:
+        Xo, ito, _ = orc.cosamp(pr.A, pr.Y, kappa)
+        Xg, it, _ = gpu_run(cs.cs_recover_cosamp, ctx, pr.Y, 256, kappa)
+    exact_check(Xg, it, Xo, ito, kappa)
+
+
+def test_admm_maximum_shape(cs):
+    pr = Problem(128, 256, 70, "powerlaw", seed=32, noise_var=1e-3)
+    Xo, _ = orc.admm(pr.A, pr.Y, 1.0, 1e-3, 0.0, 150)
+    ctx = cs.cs_create(128, 256, Phi=pr.Phi, admm_rho=1.0)
+    Xg, it, _ = gpu_run(cs.cs_recover_admm, ctx, pr.Y, 256, 1.0, 1e-3, 150, eps=0.0)
+    assert np.all(it == 150)
+    assert rel_l2(Xg, Xo) <= REL_L2_FP32
