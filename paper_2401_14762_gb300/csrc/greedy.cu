@@ -2,7 +2,8 @@
 //
 // One warp recovers one pixel at a time and takes the next pixel from a global work
 // counter when it finishes, so pixels that stop early (Delta < eps) free their warp at
-// once.  Per iteration the warp
+// once; a launch may cover several cubes (each with its own dictionary, found through a
+// table of cube descriptors), counted as one run of pixels.  Per iteration the warp
 //   1. correlates: p = A^T r (FP32, lane l owns atoms l, l+32, ...), for BIHT
 //      u = x + mu p,
 //   2. selects the G / 2 kappa / kappa largest magnitudes (ties to the lower atom):
@@ -18,12 +19,15 @@
 //      solution is refined to FP64 accuracy with FP64 residuals (an FP64 factorisation
 //      is the fallback); when |c| > M the minimum-norm solution s = A_c^T (A_c A_c^T)^{-1} y
 //      is used instead,
-//   5. prunes to kappa atoms (and, for gOMP, refits on them),
+//   5. prunes to kappa atoms by rank counting on the FP64 coefficients (and, for gOMP,
+//      refits on them),
 //   6. recomputes the residual r = y - A x and Delta = ||r - r_prev|| in FP64 (the
 //      paper's absolute eps = 1e-8 lies below FP32 resolution of r).
-// Because supports are sorted and every step is deterministic, an unchanged support
-// reproduces x bit for bit and Delta = 0 exactly, as in the paper's stopping rule.  All
-// per-pixel state sits in the warp's slice of shared memory.
+// Every step is deterministic and a support keeps its order, so an unchanged support
+// reproduces x bit for bit and Delta = 0 exactly, as in the paper's stopping rule; for the
+// same reason BIHT and CoSaMP may stop at a repeated iterate (the rest of the run is
+// periodic) and report the cap.  All per-pixel state sits in the warp's slice of shared
+// memory.
 #include <cuda_runtime.h>
 
 #include <mutex>

@@ -56,7 +56,7 @@ def test_setup_given_A_and_Psi(cs):
 
 
 # --------------------------------------------------------------------------- measure
-@pytest.mark.parametrize("M,N", [(48, 120), (80, 200), (102, 256), (3, 5)])
+@pytest.mark.parametrize("M,N", [(48, 120), (80, 200), (102, 256), (128, 256), (3, 5)])
 def test_measure(cs, M, N):
     torch = pytest.importorskip("torch")
     P = 32 * 5 + 3
@@ -359,3 +359,16 @@ def test_admm_maximum_shape(cs):
     Xg, it, _ = gpu_run(cs.cs_recover_admm, ctx, pr.Y, 256, 1.0, 1e-3, 150, eps=0.0)
     assert np.all(it == 150)
     assert rel_l2(Xg, Xo) <= REL_L2_FP32
+
+
+def test_fista_maximum_shape(cs):
+    """FP32 FISTA at M = 128, N = 256 (the BF16 request falls back to it there)."""
+    pr = Problem(128, 256, 70, "powerlaw", seed=33, noise_var=1e-3)
+    run = lambda Y: orc.fista(pr.A, Y, pr.L, 1e-3, 0.0, 120)[0]
+    Xo = run(pr.Y)
+    tol = fixed_iteration_tolerance(iterate_conditioning(run, pr.Y), 120)
+    ctx = cs.cs_create(128, 256, Phi=pr.Phi)
+    for prec in (0, 1):
+        Xg, it, _ = gpu_run(cs.cs_recover_fista, ctx, pr.Y, 256, 1e-3, 120, eps=0.0, prec=prec)
+        assert np.all(it == 120)
+        assert rel_l2(Xg, Xo) <= tol
