@@ -82,6 +82,28 @@ def oracle_sample(n_pix, threads, X_true, E, Phi):
     return out, secs, Y
 
 
+# ----------------------------------------------------------------------------- ranks
+def rank_seed(rank):
+    """Each rank recovers its own cube (pixels are independent: weak scaling)."""
+    return SEED + rank
+
+
+def max_over_ranks(t_ms, dist=None, device="cpu"):
+    """The job's step time: the slowest rank's (every rank's cube must be done)."""
+    if dist is None:
+        return t_ms
+    import torch
+    tt = torch.tensor([t_ms], device=device, dtype=torch.float64)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return float(tt.item())
+
+
+def job_value(t_ms, world):
+    """Recovered spectra per second over the whole job: every rank's pixels, five
+    algorithms each, in the slowest rank's step time."""
+    return P * len(ALGOS) * world / (t_ms * 1e-3)
+
+
 def host_cores():
     try:
         return len(os.sched_getaffinity(0))
@@ -233,7 +255,7 @@ def run_gpu(args):
     stream = torch.cuda.current_stream()
 
     # inputs of this rank's cube (pixels are independent: weak scaling over ranks)
-    seed = SEED + rank
+    seed = rank_seed(rank)
     Phi = sy.gaussian_phi(M, N, SEED)
     Xt = sy.powerlaw_coeffs_torch(P, N, seed, dev)
     E = sy.noise_torch(P, M, NOISE_VAR, seed, dev)
@@ -335,12 +357,8 @@ def run_gpu(args):
         torch.cuda.synchronize()
         full_ms[a] = (e0.elapsed_time(e1), bool(torch.equal(tmp, outs[a])))
         del tmp
-    t_step = sum(step_ms) / len(step_ms)
-    if dist:
-        tt = torch.tensor([t_step], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_step = float(tt.item())
-    value = P * len(ALGOS) * world / (t_step * 1e-3)
+    t_step = max_over_ranks(sum(step_ms) / len(step_ms), dist, dev)
+    value = job_value(t_step, world)
     kern_ms = {k: sum(v) / len(v) for k, v in per.items()}
 
     # ---- end to end: pinned host buffers through the same C calls; the library copies
