@@ -434,7 +434,9 @@ def run_gpu(args):
             "admm_fp32": lambda o: cs.cs_recover_admm(ctx, Yd, o, RHO, LAM, ITERS,
                                                       cs.make_opts(eps=EPS)),
         }
-        acc = {}
+        import oracle as orc
+        Psi = orc.dct2_psi(N)
+        acc, psnr = {}, {}
         for a, call in calls.items():
             call(Xa)
             cs.cs_sync(ctx)
@@ -442,6 +444,9 @@ def run_gpu(args):
             key = a.replace("_fp32", "")
             r = ref[key] if key in ("fista", "admm") else ref[key][0]
             acc[a] = float(np.linalg.norm(g - r) / np.linalg.norm(r))
+            # PSNR of each recovery against the true spectra (band domain f = Psi x)
+            pg, po = orc.psnr(g, Xs, Psi), orc.psnr(r, Xs, Psi)
+            psnr[a] = {"gpu_db": pg, "oracle_db": po, "delta_db": abs(pg - po)}
         f32 = sum(f32_ms) / len(f32_ms)
         kernels["fista_fp32"] = {"ms": f32, "tflops": flops["fista"] / (f32 * 1e-3) / 1e12,
                                  "frac_fp32_peak": flops["fista"] / (f32 * 1e-3) / 1e12 /
@@ -484,6 +489,7 @@ def run_gpu(args):
                 "clocks": clk.summary(),
                 "kernels": kernels,
                 "accuracy_rel_l2_vs_oracle": acc,
+                "psnr_vs_truth": psnr,
                 "accuracy_inputs": f"the oracle's FP32 measurements of the first {n_s} pixels, "
                                    "recovered by both sides with the step's options",
                 "peaks_file": {k: pk.get(k) for k in ("hbm_gbs", "bf16_tflops")}}

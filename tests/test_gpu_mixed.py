@@ -154,3 +154,30 @@ def test_admm_bf16_nonfinite_input_is_reported(cs):
     with pytest.raises(cs.CsError) as e:
         gpu_run(cs.cs_recover_admm, ctx, Y, pr.N, 1.0, 1e-3, 20, eps=0.0, prec=cs.CS_BF16)
     assert e.value.status == cs.CS_ERR_NONFINITE
+
+
+# --------------------------------------------------------------------------- PSNR
+@pytest.mark.parametrize("algo", ["fista", "admm", "gomp", "biht", "cosamp"])
+def test_psnr_matches_oracle(cs, algo):
+    """PSNR against the true spectra (band domain f = Psi x, the truth's peak) of the GPU
+    recovery within 0.05 dB of the oracle's; FISTA and ADMM on the mixed path."""
+    pr = Problem(80, 200, 32 * 10 + 3, "powerlaw", seed=8, noise_var=1e-3)
+    ctx = cs.cs_create(pr.M, pr.N, Phi=pr.Phi, admm_rho=1.0)
+    if algo == "fista":
+        Xo = orc.fista(pr.A, pr.Y, pr.L, 1e-3, 0.0, 300)[0]
+        Xg, _, _ = gpu_run(cs.cs_recover_fista, ctx, pr.Y, pr.N, 1e-3, 300, eps=0.0, prec=1)
+    elif algo == "admm":
+        Xo = orc.admm(pr.A, pr.Y, 1.0, 1e-3, 0.0, 300)[0]
+        Xg, _, _ = gpu_run(cs.cs_recover_admm, ctx, pr.Y, pr.N, 1.0, 1e-3, 300, eps=0.0, prec=1)
+    elif algo == "gomp":
+        Xo = orc.gomp(pr.A, pr.Y, 20, 4)[0]
+        Xg, _, _ = gpu_run(cs.cs_recover_gomp, ctx, pr.Y, pr.N, 20, 4)
+    elif algo == "biht":
+        Xo = orc.biht(pr.A, pr.Y, 20, 0.1)[0]
+        Xg, _, _ = gpu_run(cs.cs_recover_biht, ctx, pr.Y, pr.N, 20)
+    else:
+        Xo = orc.cosamp(pr.A, pr.Y, 20)[0]
+        Xg, _, _ = gpu_run(cs.cs_recover_cosamp, ctx, pr.Y, pr.N, 20)
+    pg, po = orc.psnr(Xg, pr.Xt), orc.psnr(Xo, pr.Xt)
+    print(f"{algo} psnr gpu {pg:.3f} oracle {po:.3f}")
+    assert abs(pg - po) <= 0.05
