@@ -75,6 +75,7 @@ def _configure(lib):
         lib.or_biht.argtypes = [i32, i32, _dp, i64, _dp, _dp, i32, dbl, dbl, i32, _ip, _dp,
                                 i32]
         lib.or_cosamp.argtypes = [i32, i32, _dp, i64, _dp, _dp, i32, dbl, i32, _ip, _dp, i32]
+        lib.or_sparsify.argtypes = [i32, _dp, i64, _dp, dbl, i32, _dp, _ip]
         lib.or_max_threads.restype = i32
         _lib = lib
     return _lib
@@ -227,6 +228,27 @@ def cosamp(A, Y, kappa, eps=1e-8, max_iters=100, threads=0):
     if rc:
         raise ValueError(f"or_cosamp failed ({rc})")
     return X, it, mg
+
+
+# --------------------------------------------------------------------------
+# Section II: sparsification pre-processing
+# --------------------------------------------------------------------------
+def sparsify(F, T, ddof=1, Psi=None):
+    """Sparsification of Section II on every pixel (row) of F (P x N spectra).
+
+    x = Psi^T f; x_i is zeroed where |x_i| - mean|x| < T std|x| (std normalised by
+    N - ddof).  Psi defaults to the orthonormal DCT-II.  Returns (X, kappa), kappa the
+    number of nonzero kept coefficients per pixel."""
+    F = _f64(F)
+    P, N = F.shape
+    Psi = dct2_psi(N) if Psi is None else _f64(Psi)
+    X = np.zeros((P, N))
+    kappa = np.zeros(P, dtype=np.int32)
+    rc = _load().or_sparsify(N, _ptr(Psi), P, _ptr(F), float(T), int(ddof), _ptr(X),
+                             _iptr(kappa))
+    if rc:
+        raise ValueError(f"or_sparsify failed ({rc})")
+    return X, kappa
 
 
 # --------------------------------------------------------------------------

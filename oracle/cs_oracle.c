@@ -31,6 +31,11 @@
  *   R8  The loop runs while Delta >= eps and fewer than max_iters iterations ran;
  *       eps = 0 gives a fixed iteration count.  The time cap t_conv is not used.
  *   R9  ADMM returns the x iterate of Algorithm 2 (the variable its residual uses).
+ *   R10 Sparsification (Section II): x = Psi^T f (Psi orthonormal, so Psi^T = Psi^{-1});
+ *       mu and sigma are the mean and the standard deviation of |x| over the N
+ *       coefficients, sigma normalised by N - ddof (ddof = 1: sample form, the default;
+ *       0: population form); x_i is zeroed when |x_i| - mu < T sigma and kept otherwise;
+ *       kappa = ||x_s||_0.
  *
  * Layout: all matrices row-major. A is M x N, X is P x N, Y is P x M.
  */
@@ -109,6 +114,42 @@ void or_measure(int M, int N, const double *A, int64_t P, const double *X, const
     if (E)
       for (int m = 0; m < M; ++m) Y[p * M + m] += E[p * M + m];
   }
+}
+
+/* ------------------------------------------------------------------------- */
+/* Sparsification pre-processing (Section II, reading R10), pixel by pixel:   */
+/* x = Psi^T f; mu = mean |x|; sigma = std |x| (N - ddof); x_i = 0 where      */
+/* |x_i| - mu < T sigma.  kappa (may be NULL) = number of nonzero kept x_i.   */
+/* ------------------------------------------------------------------------- */
+int or_sparsify(int N, const double *Psi, int64_t P, const double *F, double T, int ddof,
+                double *X, int32_t *kappa) {
+  if (N <= 0 || P < 0 || (ddof != 0 && ddof != 1)) return OR_ERR_ARG;
+  double *a = (double *)malloc(sizeof(double) * N);
+  if (!a) return OR_ERR_NOMEM;
+  for (int64_t p = 0; p < P; ++p) {
+    const double *f = F + p * N;
+    double *x = X + p * N;
+    for (int i = 0; i < N; ++i) { /* x_i = sum_n Psi[n][i] f_n */
+      double s = 0.0;
+      for (int n = 0; n < N; ++n) s += Psi[(size_t)n * N + i] * f[n];
+      x[i] = s;
+      a[i] = fabs(s);
+    }
+    double mu = 0.0;
+    for (int i = 0; i < N; ++i) mu += a[i];
+    mu /= N;
+    double ss = 0.0;
+    for (int i = 0; i < N; ++i) ss += (a[i] - mu) * (a[i] - mu);
+    double sigma = N - ddof > 0 ? sqrt(ss / (N - ddof)) : 0.0;
+    int32_t nz = 0;
+    for (int i = 0; i < N; ++i) {
+      if (a[i] - mu < T * sigma) x[i] = 0.0;
+      if (x[i] != 0.0) ++nz;
+    }
+    if (kappa) kappa[p] = nz;
+  }
+  free(a);
+  return OR_OK;
 }
 
 /* ------------------------------------------------------------------------- */

@@ -460,4 +460,67 @@ def pin_degenerate():
     assert orc.gomp(A, np.zeros((0, 10)), 4, 2)[0].shape == (0, 25)
 
 
+# --------------------------------------------------------------------------
+# Sparsification pre-processing (Section II): x = Psi^T f, zero x_i where
+# |x_i| - mean|x| < T std|x|
+# --------------------------------------------------------------------------
+def pin_sparsify_worked_example():
+    """Hand-worked cases with Psi = I (so x = f exactly).  f = (4, -2, 1, 0): mean |x|
+    = 7/4, squared deviations sum to 8.75, sample std sqrt(8.75/3) = 1.7078, population
+    std sqrt(8.75/4) = 1.4790.  Centred magnitudes (2.25, 0.25, -0.75, -1.75).
+    T = 0.15: sample threshold 0.2562 keeps index 0; population 0.2219 keeps 0 and 1.
+    T = 0 keeps 0 and 1; T = -1.1 (sample, -1.8786) keeps everything.
+    f = (3, 1, 2, -2), T = 0: mean 2, centred (1, -1, 0, 0): the entries equal to the
+    mean are kept (only |x_i| - mu < T sigma zeroes), with their signs."""
+    I4 = np.eye(4)
+    F = np.array([[4.0, -2.0, 1.0, 0.0], [3.0, 1.0, 2.0, -2.0]])
+    X, k = orc.sparsify(F, 0.15, 1, I4)
+    assert np.array_equal(X[0], [4, 0, 0, 0]) and np.array_equal(X[1], [3, 0, 0, 0])
+    assert list(k) == [1, 1]
+    X, k = orc.sparsify(F, 0.15, 0, I4)
+    assert np.array_equal(X[0], [4, -2, 0, 0]) and list(k)[0] == 2
+    X, k = orc.sparsify(F, 0.0, 1, I4)
+    assert np.array_equal(X[0], [4, -2, 0, 0])
+    assert np.array_equal(X[1], [3, 0, 2, -2]) and list(k) == [2, 3]
+    X, k = orc.sparsify(F[:1], -1.1, 1, I4)
+    assert np.array_equal(X[0], F[0]) and list(k) == [3]  # the kept 0 is not counted
+
+
+def pin_sparsify_transform():
+    """With every coefficient kept (T very negative) the output is the analysis
+    transform x = Psi^T f: for the DCT-II that is the orthonormal DCT-II of f (library
+    routine), and for a random orthogonal Psi it is Psi^T f."""
+    F = _rng(21).standard_normal((5, 200))
+    X, k = orc.sparsify(F, -1e9)
+    assert np.abs(X - scipy.fft.dct(F, type=2, norm="ortho", axis=1)).max() < 1e-12
+    assert list(k) == [200] * 5
+    Q = rand_orthogonal(40, 22)
+    F = _rng(23).standard_normal((3, 40))
+    X, _ = orc.sparsify(F, -1e9, 1, Q)
+    assert np.abs(X - F @ Q).max() < 1e-12
+
+
+def pin_sparsify_monotone_and_scale_free():
+    """Section II: a larger T keeps fewer coefficients (the kept sets are nested), and
+    scaling a spectrum scales mean and std alike, so the kept set does not change."""
+    F = sy.powerlaw_coeffs(40, 120, 24) @ orc.dct2_psi(120).T + \
+        0.01 * _rng(25).standard_normal((40, 120))
+    prev = None
+    for T in (-0.5, 0.0, 0.1, 0.5, 1.0, 2.0):
+        X, k = orc.sparsify(F, T)
+        keep = X != 0
+        if prev is not None:
+            assert np.all(keep <= prev)  # nested
+        prev = keep
+        Xs, ks = orc.sparsify(4.0 * F, T)
+        assert np.array_equal(Xs != 0, keep) and np.array_equal(ks, k)
+        assert np.abs(Xs - 4.0 * X).max() < 1e-12
+    # at T = 0 a coefficient survives exactly when its magnitude reaches the mean
+    X0, _ = orc.sparsify(F, 0.0)
+    x = scipy.fft.dct(F, type=2, norm="ortho", axis=1)
+    a = np.abs(x)
+    far = np.abs(a - a.mean(axis=1, keepdims=True)) > 1e-9
+    assert np.array_equal((X0 != 0)[far], (a >= a.mean(axis=1, keepdims=True))[far])
+
+
 ALL_PINS = [v for k, v in sorted(globals().items()) if k.startswith("pin_")]

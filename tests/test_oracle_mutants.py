@@ -44,6 +44,13 @@ MUTANTS = {
     "measure_noise_sign": ("Y[p * M + m] += E[p * M + m];", "Y[p * M + m] -= E[p * M + m];"),
     "svd_cutoff_inverted": ("if (sig[j] <= tol) continue;\n      double uty",
                             "if (sig[j] > tol) continue;\n      double uty"),
+    "sparsify_population_std": ("sqrt(ss / (N - ddof))", "sqrt(ss / N)"),
+    "sparsify_no_abs": ("      a[i] = fabs(s);", "      a[i] = s;"),
+    "sparsify_strict_keep": ("if (a[i] - mu < T * sigma) x[i] = 0.0;",
+                             "if (a[i] - mu <= T * sigma) x[i] = 0.0;"),
+    "sparsify_transposed_psi": ("s += Psi[(size_t)n * N + i] * f[n];",
+                                "s += Psi[(size_t)i * N + n] * f[n];"),
+    "sparsify_std_uncentred": ("ss += (a[i] - mu) * (a[i] - mu);", "ss += a[i] * a[i];"),
 }
 
 _RUNNER = r"""
