@@ -22,6 +22,7 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -266,11 +267,15 @@ def run_gpu(args):
     outs = {a: torch.empty((P, N), device=dev) for a in ALGOS}
     iters = {a: torch.zeros(P, device=dev, dtype=torch.int32) for a in ALGOS}
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
-    opts = {a: cs.make_opts(eps=EPS, max_iters=100, mu=MU, iters_out=iters[a]) for a in ALGOS}
+    conv = {a: torch.zeros(P, dtype=torch.uint8, device=dev) for a in ALGOS}
+    opts = {a: cs.make_opts(eps=EPS, max_iters=100, mu=MU, iters_out=iters[a],
+                            converged_out=conv[a]) for a in ALGOS}
     # FISTA runs on the tensor cores (split-BF16, mixed precision); its plain FP32 run is
     # timed beside it for the mixed-vs-FP32 comparison
-    opts["fista"] = cs.make_opts(eps=EPS, prec=cs.CS_BF16, iters_out=iters["fista"])
-    opts["admm"] = cs.make_opts(eps=EPS, prec=cs.CS_BF16, iters_out=iters["admm"])
+    opts["fista"] = cs.make_opts(eps=EPS, prec=cs.CS_BF16, iters_out=iters["fista"],
+                                 converged_out=conv["fista"])
+    opts["admm"] = cs.make_opts(eps=EPS, prec=cs.CS_BF16, iters_out=iters["admm"],
+                                converged_out=conv["admm"])
     fista32_out = torch.empty((P, N), device=dev)
     fista32_opts = cs.make_opts(eps=EPS)
     admm32_out = torch.empty((P, N), device=dev)
@@ -368,7 +373,8 @@ def run_gpu(args):
     Yh = torch.empty((P, M)).pin_memory()
     outh = {a: torch.empty((P, N)).pin_memory() for a in ALGOS}
     e2e_ms = []
-    for _ in range(max(1, min(args.steps, 2))):
+    # one untimed pass first: it allocates the library's staging buffers, a one-off
+    for rep in range(1 + max(1, min(args.steps, 2))):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         cs.cs_measure(ctx, Xh, Yh, Eh)
@@ -379,7 +385,8 @@ def run_gpu(args):
         cs.cs_recover_gomp(ctx, Yh, outh["gomp"], KAPPA, G, cs.make_opts(eps=EPS))
         cs.cs_recover_biht(ctx, Yh, outh["biht"], KAPPA, cs.make_opts(eps=EPS, mu=MU))
         cs.cs_recover_cosamp(ctx, Yh, outh["cosamp"], KAPPA, cs.make_opts(eps=EPS))
-        e2e_ms.append((time.perf_counter() - t0) * 1e3)
+        if rep > 0:
+            e2e_ms.append((time.perf_counter() - t0) * 1e3)
     e2e_t = sum(e2e_ms) / len(e2e_ms)
     h2d = P * N * 4 + P * M * 4 + len(ALGOS) * P * M * 4
     d2h = P * M * 4 + len(ALGOS) * P * N * 4
@@ -447,6 +454,26 @@ def run_gpu(args):
             # PSNR of each recovery against the true spectra (band domain f = Psi x)
             pg, po = orc.psnr(g, Xs, Psi), orc.psnr(r, Xs, Psi)
             psnr[a] = {"gpu_db": pg, "oracle_db": po, "delta_db": abs(pg - po)}
+        # Table I's columns (Section III) on this synthetic cube: PSNR against the true
+        # spectra over the whole cube, iterations, the ratio of pixels that met Delta < eps
+        # (the iteration cap stands in for the paper's wall-clock cap), recovery time
+        # orthonormal DCT-II synthesis matrix (the library's default Psi), built here
+        kk = torch.arange(N, dtype=torch.float64, device=dev)
+        C = torch.cos(math.pi * (2 * kk[None, :] + 1) * kk[:, None] / (2 * N)) * math.sqrt(2 / N)
+        C[0] /= math.sqrt(2)
+        Psi_d = C.T
+        F_true = Xt.double() @ Psi_d.T
+        peak = F_true.abs().max()
+        table1 = {}
+        for a in ALGOS:
+            mse = ((outs[a].double() @ Psi_d.T - F_true) ** 2).mean()
+            it_a = iters[a].double()
+            table1[a] = {"psnr_db": float(10 * torch.log10(peak * peak / mse)),
+                         "iters_mean": float(it_a.mean()), "iters_min": int(it_a.min()),
+                         "iters_max": int(it_a.max()),
+                         "converged_ratio": float((conv[a] == 1).double().mean()),
+                         "recovery_ms": kern_ms[a]}
+        del F_true
         f32 = sum(f32_ms) / len(f32_ms)
         kernels["fista_fp32"] = {"ms": f32, "tflops": flops["fista"] / (f32 * 1e-3) / 1e12,
                                  "frac_fp32_peak": flops["fista"] / (f32 * 1e-3) / 1e12 /
@@ -490,9 +517,12 @@ def run_gpu(args):
                 "kernels": kernels,
                 "accuracy_rel_l2_vs_oracle": acc,
                 "psnr_vs_truth": psnr,
+                "table1": table1,
                 "accuracy_inputs": f"the oracle's FP32 measurements of the first {n_s} pixels, "
                                    "recovered by both sides with the step's options",
                 "peaks_file": {k: pk.get(k) for k in ("hbm_gbs", "bf16_tflops")}}
+    if line is not None:
+        line["sparsify"] = run_sparsify(cs, ctx, Xt, dev, stream, flush)
     cs.cs_destroy(ctx)
     if rank == 0 and not args.no_batch:
         line["batch"] = run_batch(cs, sy, dev, stream, flush)
@@ -500,6 +530,54 @@ def run_gpu(args):
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
+
+
+def run_sparsify(cs, ctx, Xt, dev, stream, flush, T=0.1):
+    """The sparsification pre-processing of Section II (outside the step): the cube's
+    spectra f = Psi x + white noise (std 0.01), T = 0.1 as in the paper's experiments.
+    One FP32 transform per pixel (2 N^2 flops) with FP64-certified decisions; the
+    algorithmic traffic is F in, X out and kappa out."""
+    import torch
+    P_, N_ = Xt.shape
+    kk = torch.arange(N_, dtype=torch.float64, device=dev)
+    C = torch.cos(math.pi * (2 * kk[None, :] + 1) * kk[:, None] / (2 * N_)) * math.sqrt(2 / N_)
+    C[0] /= math.sqrt(2)
+    g = torch.Generator(device=dev)
+    g.manual_seed(SEED)
+    F = (Xt.double() @ C + 0.01 * torch.randn((P_, N_), generator=g, device=dev,
+                                             dtype=torch.float64)).float()
+    X = torch.empty_like(F)
+    kap = torch.empty(P_, dtype=torch.int16, device=dev)
+    rec = torch.zeros(1, dtype=torch.int64, device=dev)
+    for _ in range(3):
+        cs.cs_sparsify(ctx, F, X, T, 1, kap, rec)
+    ms = []
+    for _ in range(5):
+        flush.fill_(1)
+        rec.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        cs.cs_sparsify(ctx, F, X, T, 1, kap, rec)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    cs.cs_sync(ctx)
+    t = statistics.median(ms)
+    flops = 2.0 * N_ * N_ * P_
+    nbytes = P_ * (8 * N_ + 2)
+    pk = peaks()
+    return {"workload": f"{P_} spectra x N={N_}, power law + N(0, 1e-4) noise, T={T}, "
+                        "sample std",
+            "ms": t, "spectra_per_s": P_ / (t * 1e-3),
+            "tflops": flops / (t * 1e-3) / 1e12,
+            "frac_fp32_peak": flops / (t * 1e-3) / 1e12 / FP32_PEAK_TFLOPS,
+            "gbs": nbytes / (t * 1e-3) / 1e9,
+            "frac_hbm_of_measured": nbytes / (t * 1e-3) / 1e9 / pk["hbm_gbs"]
+            if pk.get("hbm_gbs") else None,
+            "pixels_decided_in_fp64": int(rec.item()),
+            "zeroed_fraction": float((X == 0).double().mean()),
+            "kappa_mean": float(kap.double().mean()),
+            "l2": "flushed before each timed run"}
 
 
 def run_batch(cs, sy, dev, stream, flush):

@@ -214,16 +214,44 @@ typedef struct {
  * context limits), P and per-pixel sparsity.  gOMP, BIHT and CoSaMP run every cube in one
  * persistent launch: warps take pixels from one counter over all cubes' pixels, so cubes
  * and pixels that finish early free their warps for the rest.  FISTA and ADMM, whose
- * per-pixel work is fixed by the iteration count, run one launch per cube.  Results
- * equal the single-cube calls' bit for bit.
+ * per-pixel work is fixed by the iteration count, run one launch per cube, largest cube
+ * first, spread over four streams of items[0].ctx that fork from its stream and join
+ * back into it (small cubes, of fewer tiles than the GPU has SMs, run side by side).
+ * Results equal the single-cube calls' bit for bit.
  * opts gives eps, max_iters, prec, mu and cycle_skip for every cube; its per-pixel
  * pointers are ignored (each item has its own).  Everything runs, asynchronously, on
  * items[0].ctx's stream; device-side conditions of the whole batch latch in items[0].ctx's
  * status word (cs_sync(items[0].ctx)).  Every context must be on the current device.
+ * CUDA graphs: the call queues only kernels, memsets and event records/waits on that
+ * stream (and the streams it forks), so once a first call with the same cubes has run
+ * (which creates the fork streams and sizes the scratch), a caller may capture the call
+ * on items[0].ctx's stream (relaxed capture mode) and replay the graph on new
+ * measurements written into the same Y buffers.
  * Argument errors (a NULL or host pointer, P < 0, kappa out of any cube's range) return
  * before anything is launched. */
 cs_status cs_recover_batch(const cs_batch_item *items, int n_items, cs_algo algo,
                            const cs_algo_params *params, const cs_opts *opts);
+
+/* Sparsification pre-processing (Section II): the paper makes each pixel kappa-sparse
+ * before it is measured.  For every pixel p (row of F, P x N spectra, FP32, row-major,
+ * device memory) the call takes x = Psi^T f to the transform domain (Psi is the
+ * context's transform, which must be orthonormal; the default DCT-II is) and zeroes
+ * x_i where |x_i| - mu < T sigma, mu and sigma the mean and the standard deviation of
+ * |x| over the N coefficients (sigma normalised by N - ddof: ddof = 1 the sample form,
+ * 0 the population form).  Larger T keeps fewer coefficients.
+ *   X            P x N output coefficients (device), ready for cs_measure.
+ *   kappa_out    optional, P entries (device): ||x_p||_0 after sparsification, usable
+ *                as kappa_per_pixel of the greedy calls.
+ *   recomputed_out optional, 1 entry (device), incremented by the number of pixels
+ *                whose decisions were taken in FP64 (see below).
+ * Every decision equals the one the FP64 definition takes: the transform runs in FP32
+ * and a pixel with a coefficient whose margin to the threshold is within the FP32
+ * error bound is recomputed in FP64.  Kept values are the FP32 (or FP64-rounded)
+ * coefficients.  Errors: CS_ERR_ARG for a context made from A (no Psi), P < 0,
+ * non-finite T, ddof other than 0/1, a NULL or host pointer; non-finite spectra latch
+ * CS_ERR_NONFINITE.  Asynchronous on the context's stream. */
+cs_status cs_sparsify(cs_ctx *ctx, const float *F, float *X, int64_t P, double T, int ddof,
+                      int16_t *kappa_out, unsigned long long *recomputed_out);
 
 /* Waits for the context's stream and returns (and clears) the latched device status. */
 cs_status cs_sync(cs_ctx *ctx);

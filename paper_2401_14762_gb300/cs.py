@@ -22,7 +22,7 @@ CS_FP32, CS_BF16, CS_FP8_E4M3 = 0, 1, 2
 EXPORTED = ["cs_opts_default", "cs_create", "cs_destroy", "cs_get_lipschitz", "cs_get_dictionary",
             "cs_measure", "cs_recover_fista", "cs_recover_admm", "cs_recover_gomp",
             "cs_recover_biht", "cs_recover_cosamp", "cs_get_work", "cs_recover_gomp_noalloc",
-            "cs_recover_batch", "cs_sync", "cs_last_error"]
+            "cs_recover_batch", "cs_sparsify", "cs_sync", "cs_last_error"]
 CS_ALGO_FISTA, CS_ALGO_ADMM, CS_ALGO_GOMP, CS_ALGO_BIHT, CS_ALGO_COSAMP = 0, 1, 2, 3, 4
 
 
@@ -81,6 +81,7 @@ def load_library(path: str = LIB_PATH):
     lib.cs_recover_gomp_noalloc.argtypes = [vp, i32, i32, vp, vp, i64, i32, i32, op, vp]
     lib.cs_recover_batch.argtypes = [ctypes.POINTER(cs_batch_item), i32, i32,
                                      ctypes.POINTER(cs_algo_params), op]
+    lib.cs_sparsify.argtypes = [vp, vp, vp, i64, dbl, i32, vp, vp]
     lib.cs_sync.argtypes = [vp]
     lib.cs_last_error.argtypes = []
     lib.cs_last_error.restype = ctypes.c_char_p
@@ -112,7 +113,7 @@ def _ptr(a, dtype=None):
             raise ValueError("tensor must be contiguous")
         if dtype is not None and a.dtype != {np.float32: torch.float32, np.float64: torch.float64,
                                             np.int32: torch.int32, np.uint8: torch.uint8,
-                                            np.int16: torch.int16}[dtype]:
+                                            np.int16: torch.int16, np.int64: torch.int64}[dtype]:
             raise TypeError(f"expected {dtype}, got {a.dtype}")
         return a.data_ptr()
     raise TypeError(f"unsupported array type {type(a)}")
@@ -215,6 +216,17 @@ def cs_measure(ctx: Context, X, Y, E=None, P=None):
     _check(load_library().cs_measure(ctx.handle, _ptr(X, np.float32), _ptr(Y, np.float32),
                                      _ptr(E, np.float32), int(P)))
     return Y
+
+
+def cs_sparsify(ctx: Context, F, X, T, ddof=1, kappa_out=None, recomputed_out=None, P=None):
+    """Sparsification of Section II: X = Psi^T F per pixel with x_i zeroed where
+    |x_i| - mean|x| < T std|x|.  F, X (P x N float32), kappa_out (P int16) and
+    recomputed_out (1 int64: pixels decided in FP64) are device tensors."""
+    P = _rows(F) if P is None else P
+    _check(load_library().cs_sparsify(ctx.handle, _ptr(F, np.float32), _ptr(X, np.float32),
+                                      int(P), float(T), int(ddof), _ptr(kappa_out, np.int16),
+                                      _ptr(recomputed_out, np.int64)))
+    return X
 
 
 def cs_recover_fista(ctx: Context, Y, X, lam, iters, opts: cs_opts | None = None, P=None):

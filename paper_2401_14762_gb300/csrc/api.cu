@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 #include <stdio.h>
 
+#include <algorithm>
 #include <cmath>
 #include <vector>
 #include <new>
@@ -48,6 +49,9 @@ void free_ctx(Ctx& c) {
   cudaFree(c.W32);
   cudaFree(c.W64);
   cudaFree(c.Wpad);
+  cudaFree(c.Psi64);
+  cudaFree(c.Psi32);
+  cudaFree(c.psi_cn);
   cudaFree(c.cube_table);
   cudaFree(c.scratch64);
   cudaFree(c.status);
@@ -58,6 +62,22 @@ void free_ctx(Ctx& c) {
   cudaFree(c.fb64);
   cudaFree(c.work);
   cudaFree(c.beta);
+  for (int k = 0; k < Ctx::kAux; ++k) {
+    if (c.aux[k]) cudaStreamDestroy(c.aux[k]);
+    if (c.ev_join[k]) cudaEventDestroy(c.ev_join[k]);
+  }
+  if (c.ev_fork) cudaEventDestroy(c.ev_fork);
+}
+
+// The fork-join streams and events of multi-cube convex batches, created once.
+cudaError_t ensure_aux(Ctx& c) {
+  if (c.ev_fork) return cudaSuccess;
+  for (int k = 0; k < Ctx::kAux; ++k) {
+    cudaError_t e = cudaStreamCreateWithFlags(&c.aux[k], cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c.ev_join[k], cudaEventDisableTiming);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaEventCreateWithFlags(&c.ev_fork, cudaEventDisableTiming);
 }
 
 // Is ptr device-accessible memory (cudaMalloc / managed)?  Host memory, pinned or not,
@@ -180,7 +200,11 @@ cs_status cs_create(cs_ctx** out, int M, int N, const double* A_host, const doub
       (e = cs::dalloc(&c.scratch64, c.scratch_elems)) != cudaSuccess ||
       (e = cs::dalloc(&c.status, 1)) != cudaSuccess ||
       (e = cs::dalloc(&c.counter, 2)) != cudaSuccess ||
-      (e = cs::dalloc(&c.work, 1)) != cudaSuccess) {
+      (e = cs::dalloc(&c.work, 1)) != cudaSuccess ||
+      (!A_host && ((e = cs::dalloc(&c.Psi64, (size_t)N * N)) != cudaSuccess ||
+                   (e = cs::dalloc(&c.Psi32, (size_t)N * 128 * ((N + 127) / 128))) !=
+                       cudaSuccess ||
+                   (e = cs::dalloc(&c.psi_cn, (size_t)N)) != cudaSuccess))) {
     cs::free_ctx(c);
     delete ctx;
     return cuda_fail(e, "cs_create allocation");
@@ -243,6 +267,30 @@ cs_status cs_measure(cs_ctx* ctx, const float* X, float* Y, const float* E, int6
   return cs::with_cube(ctx, X, Y, P, c.N, c.M, [&](const float* Xd, float* Yd) {
     return cs::launch_measure(c, Xd, Yd, Ed, P);
   });
+}
+
+cs_status cs_sparsify(cs_ctx* ctx, const float* F, float* X, int64_t P, double T, int ddof,
+                      int16_t* kappa_out, unsigned long long* recomputed_out) {
+  cs::set_error("");
+  if (cs_status s = cs::check_ctx(ctx)) return s;
+  cs::Ctx& c = ctx->c;
+  if (!c.Psi64) return arg_error("the context was made from A: it holds no transform Psi");
+  if (P < 0) return arg_error("P < 0");
+  if (!std::isfinite(T)) return arg_error("T must be finite");
+  if (ddof != 0 && ddof != 1) return arg_error("ddof must be 0 or 1");
+  if (P > ((int64_t)1 << 31) - 1) {
+    cs::set_error("P must be below 2^31");
+    return CS_ERR_SHAPE;
+  }
+  if (P > 0 && (!F || !X)) return arg_error("F or X is NULL");
+  if ((P > 0 && (!cs::is_device_ptr(F) || !cs::is_device_ptr(X))) ||
+      (kappa_out && !cs::is_device_ptr(kappa_out)) ||
+      (recomputed_out && !cs::is_device_ptr(recomputed_out)))
+    return arg_error("F, X, kappa_out and recomputed_out must be device memory");
+  if (P == 0) return CS_OK;
+  cudaError_t e = cs::launch_sparsify(c, F, X, P, T, ddof, kappa_out, recomputed_out);
+  if (e != cudaSuccess) return cuda_fail(e, "sparsify launch");
+  return CS_OK;
 }
 
 static cs_status check_common(const cs_ctx* ctx, const float* Y, float* X, int64_t P,
@@ -404,28 +452,61 @@ cs_status cs_recover_batch(const cs_batch_item* items, int n_items, cs_algo algo
     if (e != cudaSuccess) return cuda_fail(e, "batched greedy launch");
     return CS_OK;
   }
-  // FISTA / ADMM: one launch per cube on items[0]'s stream, conditions in its status word
-  for (int i = 0; i < n_items; ++i) {
-    const cs_batch_item& it = items[i];
-    if (it.P == 0) continue;
+  // FISTA / ADMM: one launch per cube, every launch reporting to items[0]'s status word.
+  // First, on items[0]'s stream, each context's shared data: the ADMM factor for this rho,
+  // FISTA's momentum table.  Then the cubes, largest first, round-robin over the fork-join
+  // streams, which start after that stream's work and which it waits for at the end: the
+  // launches of small cubes (a few tiles, far fewer than the SMs) run side by side.
+  std::vector<int> order;
+  for (int i = 0; i < n_items; ++i)
+    if (items[i].P > 0) order.push_back(i);
+  std::stable_sort(order.begin(), order.end(),
+                   [&](int a, int b) { return items[a].P > items[b].P; });
+  cudaError_t e = cudaSuccess;
+  for (int i : order) {
+    cs::Ctx& c = items[i].ctx->c;
+    cudaStream_t own_stream = c.stream;
+    c.stream = c0.stream;
+    if (algo == CS_ALGO_ADMM) {
+      if (c.rho != params->rho) e = cs::setup_admm_factor(c, params->rho);
+    } else {
+      e = cs::momentum_table(c, params->iters);
+    }
+    c.stream = own_stream;
+    if (e != cudaSuccess) return cuda_fail(e, "batched convex setup");
+  }
+  const bool fork = order.size() > 1;
+  int used = 0;
+  if (fork) {
+    e = cs::ensure_aux(c0);
+    if (e == cudaSuccess) e = cudaEventRecord(c0.ev_fork, c0.stream);
+    if (e != cudaSuccess) return cuda_fail(e, "batch fork");
+    used = (int)std::min<size_t>(order.size(), cs::Ctx::kAux);
+    for (int k = 0; k < used && e == cudaSuccess; ++k)
+      e = cudaStreamWaitEvent(c0.aux[k], c0.ev_fork, 0);
+    if (e != cudaSuccess) return cuda_fail(e, "batch fork");
+  }
+  for (size_t j = 0; j < order.size() && e == cudaSuccess; ++j) {
+    const cs_batch_item& it = items[order[j]];
     cs::Ctx& c = it.ctx->c;
     cudaStream_t own_stream = c.stream;
     int* own_status = c.status;
-    c.stream = c0.stream;
+    c.stream = fork ? c0.aux[j % cs::Ctx::kAux] : c0.stream;
     c.status = c0.status;
-    cudaError_t e = cudaSuccess;
     cs::ConvexArgs a{it.Y, it.X, it.P, params->lambda, params->rho, o.eps, params->iters,
                      it.iters_out, it.converged_out, o.prec};
-    if (algo == CS_ALGO_ADMM) {
-      if (c.rho != params->rho) e = cs::setup_admm_factor(c, params->rho);
-      if (e == cudaSuccess) e = cs::launch_admm(c, a);
-    } else {
-      e = cs::launch_fista(c, a);
-    }
+    e = algo == CS_ALGO_ADMM ? cs::launch_admm(c, a) : cs::launch_fista(c, a, false);
     c.stream = own_stream;
     c.status = own_status;
-    if (e != cudaSuccess) return cuda_fail(e, "batched convex launch");
   }
+  // join even after a failed launch, so that the context stream still follows whatever
+  // did start
+  for (int k = 0; k < used; ++k) {
+    cudaError_t ej = cudaEventRecord(c0.ev_join[k], c0.aux[k]);
+    if (ej == cudaSuccess) ej = cudaStreamWaitEvent(c0.stream, c0.ev_join[k], 0);
+    if (e == cudaSuccess) e = ej;
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "batched convex launch");
   return CS_OK;
 }
 

@@ -527,10 +527,12 @@ cudaError_t momentum_table(Ctx& c, int iters) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_fista(Ctx& c, const ConvexArgs& a) {
+cudaError_t launch_fista(Ctx& c, const ConvexArgs& a, bool table) {
   if (a.P == 0) return cudaSuccess;
-  cudaError_t e = momentum_table(c, a.iters);
-  if (e != cudaSuccess) return e;
+  if (table) {
+    cudaError_t e = momentum_table(c, a.iters);
+    if (e != cudaSuccess) return e;
+  }
   if (a.prec != CS_FP32 && fista_tc_supported(c.M, c.N)) return launch_fista_tc(c, a);
   CvParams p = base_params(c);
   p.beta = c.beta;

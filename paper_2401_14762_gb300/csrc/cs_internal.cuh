@@ -43,6 +43,9 @@ struct Ctx {
   float* W32 = nullptr;       // M x M, FP32 (A A^T + rho I)^{-1}
   double* W64 = nullptr;      // M x M, the same in FP64 (split for the tensor cores)
   float* Wpad = nullptr;      // M x smem_ld(M), the FP32 factor with zero-padded rows
+  double* Psi64 = nullptr;    // N x N transform Psi (contexts made from Phi; else NULL)
+  float* Psi32 = nullptr;     // its FP32 rounding, rows zero padded to 128 ceil(N / 128)
+  float* psi_cn = nullptr;    // column norms of Psi, rounded up to FP32
   double* scratch64 = nullptr;  // setup scratch
   size_t scratch_elems = 0;
   int* status = nullptr;      // device status word
@@ -58,6 +61,11 @@ struct Ctx {
   float* stage_out = nullptr;
   float* stage_aux = nullptr;
   size_t stage_in_bytes = 0, stage_out_bytes = 0, stage_aux_bytes = 0;
+  // fork-join streams of multi-cube FISTA/ADMM batches (created by the first such batch):
+  // ev_fork orders them after the context stream, ev_join[k] orders it after aux[k]
+  static constexpr int kAux = 4;
+  cudaStream_t aux[kAux] = {};
+  cudaEvent_t ev_fork = nullptr, ev_join[kAux] = {};
 };
 
 void set_error(const std::string& msg);
@@ -70,6 +78,10 @@ cudaError_t setup_admm_factor(Ctx& c, double rho);
 
 // ---- measurement ----
 cudaError_t launch_measure(const Ctx& c, const float* X, float* Y, const float* E, int64_t P);
+
+// ---- sparsification pre-processing (Section II) ----
+cudaError_t launch_sparsify(const Ctx& c, const float* F, float* X, int64_t P, double T,
+                            int ddof, int16_t* kappa, unsigned long long* recomputed);
 
 // ---- convex (FISTA / ADMM) ----
 struct ConvexArgs {
@@ -84,7 +96,10 @@ struct ConvexArgs {
   uint8_t* conv_out;
   cs_precision prec;
 };
-cudaError_t launch_fista(Ctx& c, const ConvexArgs& a);
+// FISTA's momentum weights beta_i (i = 1..iters) into c.beta, on c.stream
+cudaError_t momentum_table(Ctx& c, int iters);
+// table = false: c.beta already holds at least a.iters weights (batches write it once)
+cudaError_t launch_fista(Ctx& c, const ConvexArgs& a, bool table = true);
 bool fista_tc_supported(int M, int N);
 cudaError_t launch_fista_tc(const Ctx& c, const ConvexArgs& a);
 cudaError_t launch_admm(const Ctx& c, const ConvexArgs& a);

@@ -207,6 +207,25 @@ __global__ void k_pad_rows(int rows, int cols, int ld, const float* src, float* 
   }
 }
 
+// dst (rows x ld, FP32) = src (rows x cols, FP64) rounded, each row zero padded to ld
+__global__ void k_cast_pad_f32(int rows, int cols, int ld, const double* src, float* dst) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < rows * ld) {
+    int r = i / ld, c = i - r * ld;
+    dst[i] = c < cols ? (float)src[(size_t)r * cols + c] : 0.f;
+  }
+}
+
+// cn[i] = ||Psi(:, i)||_2 in FP64, rounded up to FP32 (an upper bound for error bounds)
+__global__ void k_col_norms(int N, const double* Psi, float* cn) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < N) {
+    double s = 0.0;
+    for (int n = 0; n < N; ++n) s += Psi[(size_t)n * N + i] * Psi[(size_t)n * N + i];
+    cn[i] = __double2float_ru(sqrt(s) * (1.0 + 1e-12));
+  }
+}
+
 __global__ void k_add_diag(int n, double* K, double v) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) K[i * n + i] += v;
@@ -238,6 +257,13 @@ cudaError_t setup_dictionary(Ctx& c, const double* A_host, const double* Phi_hos
       k_dct_psi<<<nblk(N * N, 256), 256, 0, s>>>(N, Psi);
     }
     k_gemm_f64<<<nblk(M * N, 256), 256, 0, s>>>(M, N, N, Phi, N, 1, Psi, N, 1, c.A64);
+    if (c.Psi64) {  // kept for the sparsification pre-processing
+      e = cudaMemcpyAsync(c.Psi64, Psi, sizeof(double) * N * N, cudaMemcpyDeviceToDevice, s);
+      if (e != cudaSuccess) return e;
+      const int ldp = 128 * ((N + 127) / 128);
+      k_cast_pad_f32<<<nblk(N * ldp, 256), 256, 0, s>>>(N, N, ldp, Psi, c.Psi32);
+      k_col_norms<<<nblk(N, 256), 256, 0, s>>>(N, Psi, c.psi_cn);
+    }
   }
   k_transpose_f64<<<nblk(M * N, 256), 256, 0, s>>>(M, N, c.A64, c.At64);
   // Gram A^T A (N x N): (A^T)(i,k) = A[k*N + i]

@@ -158,3 +158,67 @@ def test_batch_many_small_cubes(cs):
         Xs, its, _ = gpu_run(cs.cs_recover_cosamp, ctx, pr.Y, 120, 6)
         assert np.array_equal(X.cpu().numpy().view(np.uint32), Xs.view(np.uint32))
         assert np.array_equal(it.cpu().numpy(), its)
+
+
+@pytest.mark.parametrize("algo", ["cosamp", "fista"])
+def test_batch_replays_in_cuda_graph(cs, algo):
+    """cs_recover_batch queues only stream-ordered work (kernels, memsets, and event waits
+    that fork its per-cube FISTA/ADMM launches over several streams and join them back),
+    so it can be captured in a CUDA graph: replaying the graph on new measurements in the
+    same buffers gives, bit for bit, what a direct call gives on them."""
+    torch = torch_cuda()
+    s = torch.cuda.Stream()
+    kind = "sparse" if algo == "cosamp" else "powerlaw"
+    shapes, first = _cubes(kind)
+    second = [Problem(M, N, P, kind, seed=80 + i, S=6, amplitude="separated") if P else None
+              for i, (M, N, P) in enumerate(shapes)]
+    ctxs = [cs.cs_create(M, N, Phi=pr.Phi if pr else sy.gaussian_phi(M, N, 1),
+                         stream=s.cuda_stream) for (M, N, _), pr in zip(shapes, first)]
+    # the second set reuses each cube's dictionary: measure it with the first set's A
+    Ys, Xs, its = [], [], []
+    for (M, N, P), pr in zip(shapes, first):
+        Ys.append(torch.zeros((P, M), device="cuda"))
+        Xs.append(torch.zeros((P, N), device="cuda"))
+        its.append(torch.zeros((P,), device="cuda", dtype=torch.int32))
+    items = [{"ctx": c, "Y": Y, "X": X, "iters_out": it if Y.shape[0] else None}
+             for c, Y, X, it in zip(ctxs, Ys, Xs, its)]
+
+    def call():
+        if algo == "cosamp":
+            cs.cs_recover_batch(items, cs.CS_ALGO_COSAMP, kappa=12, opts=cs.make_opts())
+        else:
+            cs.cs_recover_batch(items, cs.CS_ALGO_FISTA, lam=1e-3, iters=80,
+                                opts=cs.make_opts(eps=0.0, prec=1))
+
+    def load(probs):
+        torch.cuda.synchronize()
+        for Y, pr, p1 in zip(Ys, probs, first):
+            if pr is not None:
+                Y.copy_(torch.from_numpy(orc.measure(p1.A, pr.Xt).astype(np.float32)))
+        torch.cuda.synchronize()
+
+    def outputs():
+        torch.cuda.synchronize()
+        return [(X.cpu().numpy().copy(), it.cpu().numpy().copy()) for X, it in zip(Xs, its)]
+
+    load(first)
+    with torch.cuda.stream(s):
+        call()  # warm-up: creates the fork-join streams, sizes the greedy scratch
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s, capture_error_mode="relaxed"):
+        call()
+    cs.cs_sync(ctxs[0])
+    for probs in (second, first):
+        load(probs)
+        g.replay()
+        replayed = outputs()
+        with torch.cuda.stream(s):
+            call()
+        cs.cs_sync(ctxs[0])
+        direct = outputs()
+        for (Xg, ig), (Xd, idd), (M, N, P) in zip(replayed, direct, shapes):
+            assert np.array_equal(Xg.view(np.uint32), Xd.view(np.uint32))
+            assert np.array_equal(ig, idd)
+            if P:
+                assert np.isfinite(Xd).all() and (idd > 0).all()

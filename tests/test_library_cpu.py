@@ -59,3 +59,5 @@ def test_errors_before_any_device_work(lib):
     assert lib.cs_recover_batch(items, 0, cs.CS_ALGO_GOMP, ctypes.byref(prm), None) == cs.CS_ERR_ARG
     assert lib.cs_recover_batch(items, 1, cs.CS_ALGO_GOMP, None, None) == cs.CS_ERR_ARG
     assert lib.cs_recover_batch(items, 1, 7, ctypes.byref(prm), None) == cs.CS_ERR_ARG
+    # sparsification: a NULL context is an argument error
+    assert lib.cs_sparsify(None, None, None, 0, 0.1, 1, None, None) == cs.CS_ERR_ARG
