@@ -388,6 +388,7 @@ def run_gpu(args):
         if rep > 0:
             e2e_ms.append((time.perf_counter() - t0) * 1e3)
     e2e_t = sum(e2e_ms) / len(e2e_ms)
+    push = run_pushbroom(cs, ctx, Yh, outh) if rank == 0 else None
     h2d = P * N * 4 + P * M * 4 + len(ALGOS) * P * M * 4
     d2h = P * M * 4 + len(ALGOS) * P * N * 4
 
@@ -518,6 +519,7 @@ def run_gpu(args):
                 "accuracy_rel_l2_vs_oracle": acc,
                 "psnr_vs_truth": psnr,
                 "table1": table1,
+                "pushbroom": push,
                 "accuracy_inputs": f"the oracle's FP32 measurements of the first {n_s} pixels, "
                                    "recovered by both sides with the step's options",
                 "peaks_file": {k: pk.get(k) for k in ("hbm_gbs", "bf16_tflops")}}
@@ -530,6 +532,49 @@ def run_gpu(args):
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
+
+
+def run_pushbroom(cs, ctx, Yh, outh, lines=64):
+    """Pushbroom mode (Section II): each recovery of the cube from pinned host memory,
+    once as one host-pointer call (copy in, recover, copy out) and once streamed in
+    chunks of `lines` sensor lines with copies overlapping the recoveries
+    (cs_recover_stream).  Wall-clock per call, after one untimed call of each."""
+    chunk = lines * SIDE
+    calls = {
+        "fista": (cs.CS_ALGO_FISTA, dict(lam=LAM, iters=ITERS),
+                  cs.make_opts(eps=EPS, prec=cs.CS_BF16),
+                  lambda o: cs.cs_recover_fista(ctx, Yh, o, LAM, ITERS,
+                                                cs.make_opts(eps=EPS, prec=cs.CS_BF16))),
+        "admm": (cs.CS_ALGO_ADMM, dict(lam=LAM, rho=RHO, iters=ITERS),
+                 cs.make_opts(eps=EPS, prec=cs.CS_BF16),
+                 lambda o: cs.cs_recover_admm(ctx, Yh, o, RHO, LAM, ITERS,
+                                              cs.make_opts(eps=EPS, prec=cs.CS_BF16))),
+        "gomp": (cs.CS_ALGO_GOMP, dict(kappa=KAPPA, G=G), cs.make_opts(eps=EPS),
+                 lambda o: cs.cs_recover_gomp(ctx, Yh, o, KAPPA, G, cs.make_opts(eps=EPS))),
+        "biht": (cs.CS_ALGO_BIHT, dict(kappa=KAPPA), cs.make_opts(eps=EPS, mu=MU),
+                 lambda o: cs.cs_recover_biht(ctx, Yh, o, KAPPA, cs.make_opts(eps=EPS, mu=MU))),
+        "cosamp": (cs.CS_ALGO_COSAMP, dict(kappa=KAPPA), cs.make_opts(eps=EPS),
+                   lambda o: cs.cs_recover_cosamp(ctx, Yh, o, KAPPA, cs.make_opts(eps=EPS))),
+    }
+    out = {"chunk_pixels": chunk, "lines_per_chunk": lines}
+    for a, (code, prm, opts, whole) in calls.items():
+        o = outh[a]
+        res = {}
+        for mode in ("whole", "stream"):
+            for rep in range(2):
+                t0 = time.perf_counter()
+                if mode == "whole":
+                    whole(o)
+                else:
+                    cs.cs_recover_stream(ctx, code, Yh, o, chunk, opts=opts, **prm)
+                if rep:
+                    res[mode + "_ms"] = (time.perf_counter() - t0) * 1e3
+        out[a] = res
+    out["stream_spectra_per_s"] = len(calls) * Yh.shape[0] / (
+        sum(out[a]["stream_ms"] for a in calls) * 1e-3)
+    out["whole_spectra_per_s"] = len(calls) * Yh.shape[0] / (
+        sum(out[a]["whole_ms"] for a in calls) * 1e-3)
+    return out
 
 
 def run_sparsify(cs, ctx, Xt, dev, stream, flush, T=0.1):

@@ -232,6 +232,21 @@ typedef struct {
 cs_status cs_recover_batch(const cs_batch_item *items, int n_items, cs_algo algo,
                            const cs_algo_params *params, const cs_opts *opts);
 
+/* Pushbroom streaming (Section II: a pushbroom sensor delivers a frame of pixels at a
+ * time, and per-pixel recovery needs none of the rest of the cube).  Recovers a cube
+ * held in HOST memory (Y: P x M, X: P x N, row-major; pinned memory lets the copies
+ * overlap) in chunks of chunk_pixels pixels (a number of sensor lines): while chunk k is
+ * recovered, chunk k + 1 is copied in and chunk k - 1 copied out, through two device
+ * buffers per direction (context-owned, grown on demand).  FISTA/ADMM chunks alternate
+ * between two compute streams; gOMP/BIHT/CoSaMP chunks run in order on one.  algo and
+ * params as in cs_recover_batch; opts as in the single-cube calls, its per-pixel arrays
+ * (device, P entries) indexed by the pixel's position in the whole cube.  Results equal
+ * the single-cube call's bit for bit.  Returns once X is in host memory.  Errors: as the
+ * single-cube calls, plus CS_ERR_ARG for device Y or X or chunk_pixels < 1. */
+cs_status cs_recover_stream(cs_ctx *ctx, cs_algo algo, const cs_algo_params *params,
+                            const float *Y, float *X, int64_t P, int64_t chunk_pixels,
+                            const cs_opts *opts);
+
 /* Sparsification pre-processing (Section II): the paper makes each pixel kappa-sparse
  * before it is measured.  For every pixel p (row of F, P x N spectra, FP32, row-major,
  * device memory) the call takes x = Psi^T f to the transform domain (Psi is the

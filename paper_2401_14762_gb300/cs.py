@@ -22,7 +22,8 @@ CS_FP32, CS_BF16, CS_FP8_E4M3 = 0, 1, 2
 EXPORTED = ["cs_opts_default", "cs_create", "cs_destroy", "cs_get_lipschitz", "cs_get_dictionary",
             "cs_measure", "cs_recover_fista", "cs_recover_admm", "cs_recover_gomp",
             "cs_recover_biht", "cs_recover_cosamp", "cs_get_work", "cs_recover_gomp_noalloc",
-            "cs_recover_batch", "cs_sparsify", "cs_sync", "cs_last_error"]
+            "cs_recover_batch", "cs_recover_stream", "cs_sparsify", "cs_sync",
+            "cs_last_error"]
 CS_ALGO_FISTA, CS_ALGO_ADMM, CS_ALGO_GOMP, CS_ALGO_BIHT, CS_ALGO_COSAMP = 0, 1, 2, 3, 4
 
 
@@ -82,6 +83,8 @@ def load_library(path: str = LIB_PATH):
     lib.cs_recover_batch.argtypes = [ctypes.POINTER(cs_batch_item), i32, i32,
                                      ctypes.POINTER(cs_algo_params), op]
     lib.cs_sparsify.argtypes = [vp, vp, vp, i64, dbl, i32, vp, vp]
+    lib.cs_recover_stream.argtypes = [vp, i32, ctypes.POINTER(cs_algo_params), vp, vp, i64,
+                                      i64, op]
     lib.cs_sync.argtypes = [vp]
     lib.cs_last_error.argtypes = []
     lib.cs_last_error.restype = ctypes.c_char_p
@@ -270,6 +273,19 @@ def cs_recover_batch(items, algo, lam=0.0, rho=1.0, iters=0, kappa=0, G=0,
     prm = cs_algo_params(float(lam), float(rho), int(iters), int(kappa), int(G))
     _check(load_library().cs_recover_batch(arr, len(items), int(algo), ctypes.byref(prm),
                                            ctypes.byref(opts) if opts else None))
+
+
+def cs_recover_stream(ctx: Context, algo, Y, X, chunk_pixels, lam=0.0, rho=1.0, iters=0,
+                      kappa=0, G=0, opts: cs_opts | None = None, P=None):
+    """Pushbroom recovery of a cube in host memory (numpy arrays or CPU tensors, pinned for
+    overlap), chunk_pixels pixels at a time, double-buffered through the device."""
+    P = _rows(Y) if P is None else P
+    prm = cs_algo_params(float(lam), float(rho), int(iters), int(kappa), int(G))
+    _check(load_library().cs_recover_stream(ctx.handle, int(algo), ctypes.byref(prm),
+                                            _ptr(Y, np.float32), _ptr(X, np.float32), int(P),
+                                            int(chunk_pixels),
+                                            ctypes.byref(opts) if opts else None))
+    return X
 
 
 def cs_recover_biht(ctx: Context, Y, X, kappa, opts: cs_opts | None = None, P=None):

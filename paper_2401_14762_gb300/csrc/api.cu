@@ -67,6 +67,38 @@ void free_ctx(Ctx& c) {
     if (c.ev_join[k]) cudaEventDestroy(c.ev_join[k]);
   }
   if (c.ev_fork) cudaEventDestroy(c.ev_fork);
+  for (int b = 0; b < 2; ++b) {
+    cudaFree(c.pipe_y[b]);
+    cudaFree(c.pipe_x[b]);
+    if (c.ev_in[b]) cudaEventDestroy(c.ev_in[b]);
+    if (c.ev_comp[b]) cudaEventDestroy(c.ev_comp[b]);
+    if (c.ev_out[b]) cudaEventDestroy(c.ev_out[b]);
+  }
+}
+
+// The double buffers (chunks of `pixels`) and events of streamed recoveries.
+cudaError_t ensure_pipe(Ctx& c, int64_t pixels) {
+  cudaError_t e = cudaSuccess;
+  if (!c.ev_in[0])
+    for (int b = 0; b < 2 && e == cudaSuccess; ++b) {
+      e = cudaEventCreateWithFlags(&c.ev_in[b], cudaEventDisableTiming);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c.ev_comp[b], cudaEventDisableTiming);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c.ev_out[b], cudaEventDisableTiming);
+    }
+  if (e != cudaSuccess || c.pipe_cap >= pixels) return e;
+  for (int b = 0; b < 2; ++b) {
+    cudaFree(c.pipe_y[b]);
+    cudaFree(c.pipe_x[b]);
+    c.pipe_y[b] = c.pipe_x[b] = nullptr;
+  }
+  c.pipe_cap = 0;
+  for (int b = 0; b < 2 && e == cudaSuccess; ++b) {
+    e = cudaMalloc(reinterpret_cast<void**>(&c.pipe_y[b]), sizeof(float) * pixels * c.M);
+    if (e == cudaSuccess)
+      e = cudaMalloc(reinterpret_cast<void**>(&c.pipe_x[b]), sizeof(float) * pixels * c.N);
+  }
+  if (e == cudaSuccess) c.pipe_cap = pixels;
+  return e;
 }
 
 // The fork-join streams and events of multi-cube convex batches, created once.
@@ -507,6 +539,96 @@ cs_status cs_recover_batch(const cs_batch_item* items, int n_items, cs_algo algo
     if (e == cudaSuccess) e = ej;
   }
   if (e != cudaSuccess) return cuda_fail(e, "batched convex launch");
+  return CS_OK;
+}
+
+cs_status cs_recover_stream(cs_ctx* ctx, cs_algo algo, const cs_algo_params* params,
+                            const float* Y, float* X, int64_t P, int64_t chunk_pixels,
+                            const cs_opts* opts) {
+  cs::set_error("");
+  if (!params) return arg_error("params is NULL");
+  if (algo < CS_ALGO_FISTA || algo > CS_ALGO_COSAMP) return arg_error("unknown algorithm");
+  cs_opts o;
+  cs_opts_default(&o);
+  if (opts) o = *opts;
+  if (cs_status s = check_common(ctx, Y, X, P, &o)) return s;
+  if (chunk_pixels < 1) return arg_error("chunk_pixels < 1");
+  cs::Ctx& c = ctx->c;
+  const bool is_greedy = algo >= CS_ALGO_GOMP;
+  const int kappa = params->kappa, G = params->G;
+  if (is_greedy) {
+    if (kappa < 0 || kappa > c.N) return arg_error("kappa out of range");
+    if (algo == CS_ALGO_COSAMP && 2 * kappa > c.N) return arg_error("CoSaMP needs 2 kappa <= N");
+    if (algo == CS_ALGO_GOMP && (G < 0 || G > c.N || (G == 0 && !o.kappa_per_pixel)))
+      return arg_error("G must be in 1..N (0 only with kappa_per_pixel)");
+    if (algo == CS_ALGO_BIHT && !std::isfinite(o.mu)) return arg_error("mu must be finite");
+  } else {
+    if (!(params->lambda >= 0.0) || !std::isfinite(params->lambda))
+      return arg_error("lambda must be >= 0");
+    if (params->iters < 0) return arg_error("iters < 0");
+    if (algo == CS_ALGO_ADMM && (!(params->rho > 0.0) || !std::isfinite(params->rho)))
+      return arg_error("rho must be > 0");
+  }
+  if (P == 0) return CS_OK;
+  if (cs::is_device_ptr(Y) || cs::is_device_ptr(X))
+    return arg_error("cs_recover_stream takes Y and X in host memory");
+  const int64_t C = std::min(chunk_pixels, P);
+  cudaError_t e = cs::ensure_aux(c);
+  if (e == cudaSuccess) e = cs::ensure_pipe(c, C);
+  if (e != cudaSuccess) return cuda_fail(e, "stream buffers");
+  // per-call data every chunk reads, on the context stream before the fork
+  if (algo == CS_ALGO_ADMM && c.rho != params->rho) e = cs::setup_admm_factor(c, params->rho);
+  if (algo == CS_ALGO_FISTA) e = cs::momentum_table(c, params->iters);
+  if (e == cudaSuccess) e = cudaEventRecord(c.ev_fork, c.stream);
+  for (int k = 0; k < cs::Ctx::kAux && e == cudaSuccess; ++k)
+    e = cudaStreamWaitEvent(c.aux[k], c.ev_fork, 0);
+  if (e != cudaSuccess) return cuda_fail(e, "stream fork");
+  // copy-in on aux[0], copy-out on aux[1]; the FISTA/ADMM chunks alternate between two
+  // compute streams, the greedy ones share one (the persistent kernel's pixel counter
+  // and fallback slots belong to the context)
+  cudaStream_t s_in = c.aux[0], s_out = c.aux[1], own = c.stream;
+  const cs::GreedyAlgo ga =
+      algo == CS_ALGO_GOMP ? cs::kGomp : (algo == CS_ALGO_BIHT ? cs::kBiht : cs::kCosamp);
+  int64_t off = 0;
+  for (int k = 0; off < P && e == cudaSuccess; ++k, off += C) {
+    const int b = k & 1;
+    const int64_t n = std::min(C, P - off);
+    cudaStream_t s_comp = c.aux[is_greedy ? 2 : 2 + b];
+    if (k >= 2) e = cudaStreamWaitEvent(s_in, c.ev_out[b], 0);  // buffer b copied out
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(c.pipe_y[b], Y + off * c.M, sizeof(float) * n * c.M,
+                          cudaMemcpyHostToDevice, s_in);
+    if (e == cudaSuccess) e = cudaEventRecord(c.ev_in[b], s_in);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s_comp, c.ev_in[b], 0);
+    if (e != cudaSuccess) break;
+    int32_t* it = o.iters_out ? o.iters_out + off : nullptr;
+    uint8_t* cv = o.converged_out ? o.converged_out + off : nullptr;
+    c.stream = s_comp;
+    if (is_greedy) {
+      const int16_t* kp = o.kappa_per_pixel ? o.kappa_per_pixel + off : nullptr;
+      cs::GreedyArgs a{c.pipe_y[b], c.pipe_x[b], n, kappa, algo == CS_ALGO_GOMP ? G : 0,
+                       o.mu, o.eps, o.max_iters, kp, kappa, it, cv, o.prec,
+                       o.cycle_skip != 0};
+      e = cs::launch_greedy(c, ga, a);
+    } else {
+      cs::ConvexArgs a{c.pipe_y[b], c.pipe_x[b], n, params->lambda, params->rho, o.eps,
+                       params->iters, it, cv, o.prec};
+      e = algo == CS_ALGO_ADMM ? cs::launch_admm(c, a) : cs::launch_fista(c, a, false);
+    }
+    c.stream = own;
+    if (e == cudaSuccess) e = cudaEventRecord(c.ev_comp[b], s_comp);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s_out, c.ev_comp[b], 0);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(X + off * c.N, c.pipe_x[b], sizeof(float) * n * c.N,
+                          cudaMemcpyDeviceToHost, s_out);
+    if (e == cudaSuccess) e = cudaEventRecord(c.ev_out[b], s_out);
+  }
+  // the last copy-out follows every compute and copy-in: join it, then wait for it
+  cudaError_t ej = cudaEventRecord(c.ev_join[1], s_out);
+  if (ej == cudaSuccess) ej = cudaStreamWaitEvent(c.stream, c.ev_join[1], 0);
+  if (e == cudaSuccess) e = ej;
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c.stream);
+  if (e != cudaSuccess) return cuda_fail(e, "streamed recovery");
   return CS_OK;
 }
 

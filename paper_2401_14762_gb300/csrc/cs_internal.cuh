@@ -66,6 +66,12 @@ struct Ctx {
   static constexpr int kAux = 4;
   cudaStream_t aux[kAux] = {};
   cudaEvent_t ev_fork = nullptr, ev_join[kAux] = {};
+  // double-buffered staging of streamed (pushbroom) recoveries: chunk buffers of
+  // pipe_cap pixels and the events of their copy-in, compute and copy-out
+  float* pipe_y[2] = {};
+  float* pipe_x[2] = {};
+  int64_t pipe_cap = 0;
+  cudaEvent_t ev_in[2] = {}, ev_comp[2] = {}, ev_out[2] = {};
 };
 
 void set_error(const std::string& msg);
