@@ -48,7 +48,8 @@ SM_COUNT, SM_MAX_MHZ = 152, 2070.0
 FP32_PEAK_TFLOPS = SM_COUNT * 128 * 2 * SM_MAX_MHZ * 1e6 / 1e12
 FP64_PEAK_TFLOPS = 1.25
 KERNEL_FILES = {"fista": "fista_tc.cu", "admm": "admm_tc.cu", "measure": "convex_f32.cu",
-                "gomp": "greedy.cu", "biht": "greedy.cu", "cosamp": "greedy.cu"}
+                "gomp": "greedy.cu", "biht": "greedy.cu", "cosamp": "greedy.cu",
+                "sparsify": "sparsify.cu"}
 
 
 def config(extra=None):
@@ -512,8 +513,9 @@ def run_gpu(args):
                                            f"{secs:.1f} s"},
                 "e2e": {"value": P * len(ALGOS) / (e2e_t * 1e-3), "unit": UNIT,
                         "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-                # measure, FISTA momentum table + FISTA, ADMM, gOMP, BIHT, CoSaMP
-                "gpu_launches": 7 * args.steps,
+                # measure, FISTA momentum table + FISTA, ADMM, and for each of gOMP, BIHT
+                # and CoSaMP its cube-descriptor upload + the recovery kernel
+                "gpu_launches": 10 * args.steps,
                 "clocks": clk.summary(),
                 "kernels": kernels,
                 "accuracy_rel_l2_vs_oracle": acc,
@@ -619,6 +621,8 @@ def run_sparsify(cs, ctx, Xt, dev, stream, flush, T=0.1):
             "gbs": nbytes / (t * 1e-3) / 1e9,
             "frac_hbm_of_measured": nbytes / (t * 1e-3) / 1e9 / pk["hbm_gbs"]
             if pk.get("hbm_gbs") else None,
+            "traffic": measured_traffic("sparsify"),
+            "algorithmic_bytes": nbytes,
             "pixels_decided_in_fp64": int(rec.item()),
             "zeroed_fraction": float((X == 0).double().mean()),
             "kappa_mean": float(kap.double().mean()),
@@ -744,7 +748,17 @@ def run_only(args):
         "gomp": lambda: cs.cs_recover_gomp(ctx, Y, X, KAPPA, G, cs.make_opts(eps=EPS)),
         "biht": lambda: cs.cs_recover_biht(ctx, Y, X, KAPPA, cs.make_opts(eps=EPS, mu=MU)),
         "cosamp": lambda: cs.cs_recover_cosamp(ctx, Y, X, KAPPA, cs.make_opts(eps=EPS)),
+        # the sparsification pre-processing on spectra f = Psi x (here X holds f)
+        "sparsify": lambda: cs.cs_sparsify(ctx, F, X, 0.1, 1),
     }
+    if args.only == "sparsify":
+        kk = torch.arange(N, dtype=torch.float64, device=dev)
+        C = torch.cos(math.pi * (2 * kk[None, :] + 1) * kk[:, None] / (2 * N)) * math.sqrt(2 / N)
+        C[0] /= math.sqrt(2)
+        g = torch.Generator(device=dev)
+        g.manual_seed(SEED)
+        F = (Xt.double() @ C + 0.01 * torch.randn((n, N), generator=g, device=dev,
+                                                 dtype=torch.float64)).float()
     for _ in range(2):
         calls[args.only]()
     cs.cs_sync(ctx)
@@ -761,7 +775,7 @@ def main():
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--only", default=None,
                     choices=["measure", "fista", "fista_fp32", "admm", "admm_fp32", "gomp",
-                             "biht", "cosamp"])
+                             "biht", "cosamp", "sparsify"])
     ap.add_argument("--pixels", type=int, default=16384)
     ap.add_argument("--no-batch", action="store_true",
                     help="skip the 64-cube batching measurement")

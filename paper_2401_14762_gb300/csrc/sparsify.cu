@@ -47,16 +47,20 @@ __device__ __noinline__ void sparsify_fp64(const SpParams& p, const float* f, in
                                            int lane) {
   const int N = p.N;
   double xv[kMaxN / 32];  // this lane's coefficients i = lane, lane + 32, ...
+#pragma unroll
+  for (int j = 0; j < kMaxN / 32; ++j) xv[j] = 0.0;
+  // row by row: each row's loads are independent of the running sums, so they overlap
+#pragma unroll 4
+  for (int n = 0; n < N; ++n) {
+    const double fv = (double)f[n];
+    const double* row = p.Psi64 + (size_t)n * N;
+#pragma unroll
+    for (int j = 0; j < kMaxN / 32; ++j)
+      if (lane + 32 * j < N) xv[j] = fma(__ldg(row + lane + 32 * j), fv, xv[j]);
+  }
   double s1 = 0.0;
 #pragma unroll
-  for (int j = 0; j < kMaxN / 32; ++j) {
-    const int i = lane + 32 * j;
-    double x = 0.0;
-    if (i < N)
-      for (int n = 0; n < N; ++n) x = fma(p.Psi64[(size_t)n * N + i], (double)f[n], x);
-    xv[j] = x;
-    s1 += fabs(x);
-  }
+  for (int j = 0; j < kMaxN / 32; ++j) s1 += fabs(xv[j]);  // zero past N
   const double mu = warp_sum(s1) / N;
   double s2 = 0.0;
 #pragma unroll
@@ -123,6 +127,11 @@ __global__ void __launch_bounds__(kSpWarps * 32, 2) k_sparsify(SpParams p) {
     for (int i = 0; i < kSpPix; ++i)
 #pragma unroll
       for (int s = 0; s < S; ++s) acc[i][s] = 0.f;
+    // Psi's row n + 1 is requested before row n's products (one row of lookahead)
+    const float4* prow = reinterpret_cast<const float4*>(p.Psi32) + lane;
+    float4 nx[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) nx[q] = __ldg(prow + 32 * q);
     for (int n0 = 0; n0 < N; n0 += kSpBlock) {
       float part[kSpPix][S];
 #pragma unroll
@@ -134,12 +143,14 @@ __global__ void __launch_bounds__(kSpWarps * 32, 2) k_sparsify(SpParams p) {
         float ps[S];
 #pragma unroll
         for (int q = 0; q < NQ; ++q) {
-          const float4 v = __ldg(reinterpret_cast<const float4*>(p.Psi32 + (size_t)n * ldp +
-                                                                 128 * q) + lane);
-          ps[4 * q] = v.x;
-          ps[4 * q + 1] = v.y;
-          ps[4 * q + 2] = v.z;
-          ps[4 * q + 3] = v.w;
+          ps[4 * q] = nx[q].x;
+          ps[4 * q + 1] = nx[q].y;
+          ps[4 * q + 2] = nx[q].z;
+          ps[4 * q + 3] = nx[q].w;
+        }
+        if (n + 1 < N) {
+#pragma unroll
+          for (int q = 0; q < NQ; ++q) nx[q] = __ldg(prow + (size_t)(n + 1) * (ldp / 4) + 32 * q);
         }
 #pragma unroll
         for (int i = 0; i < kSpPix; ++i) {
