@@ -39,18 +39,21 @@ struct AtcParams {
   int32_t* iters_out;
   uint8_t* conv_out;
   int* status;
+  int inject_timeout;  // test hook: the first product is not issued (see launch_admm_tc)
 };
 
 // Issues one split product (thread 0) after the operand region is complete, and waits
-// for it; false if the wait ran out.
+// for it; false if the wait ran out.  issue = false leaves the product out (fault
+// injection: the wait then runs out).
 __device__ __forceinline__ bool tile_product(uint64_t* mbar, uint32_t& phase, uint32_t d,
                                              uint32_t o, uint32_t bh, uint32_t bl, int K,
-                                             int S, bool b_mn, uint32_t idesc) {
+                                             int S, bool b_mn, uint32_t idesc,
+                                             bool issue = true) {
   tc::fence_async_smem();
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
-  if (threadIdx.x == 0) {
+  if (threadIdx.x == 0 && issue) {
     tc::split_product(d, o, bh, bl, K, S, b_mn, idesc);
     tc::mma_commit(mbar);
   }
@@ -163,7 +166,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_admm_tc(AtcParams p) {
           }
         }
       }
-      if (!tile_product(&mbar, phase, tR, uO, uAh, uAl, Np, S, false, id1)) {
+      if (!tile_product(&mbar, phase, tR, uO, uAh, uAl, Np, S, false, id1,
+                        !(p.inject_timeout && i == 1))) {
         failed = true;
         break;
       }
@@ -268,9 +272,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_admm_tc(AtcParams p) {
     }
   }
   if (failed) {
-    // a product never completed: report, give it one more bounded wait, then release TMEM
+    // a product never completed: report, give it one more bounded wait (tile_product has
+    // already advanced the phase past it), then release TMEM
     if (tid == 0) atomicOr(p.status, kStTimeout);
-    tc::mbar_wait(&mbar, phase, kWaitLimitNs);
+    tc::mbar_wait(&mbar, phase ^ 1u, kWaitLimitNs);
   }
   tc::fence_before_sync();
   __syncthreads();
@@ -325,6 +330,7 @@ cudaError_t launch_admm_tc(const Ctx& c, const ConvexArgs& a) {
   p.iters_out = a.iters_out;
   p.conv_out = a.conv_out;
   p.status = c.status;
+  p.inject_timeout = tc::inject_timeout();
   if (a.P == 0) return cudaSuccess;
   // at least 120 KB so that one CTA (which takes all 512 TMEM columns) runs per SM
   size_t smem = admm_tc_smem(p.Mp, p.Np);

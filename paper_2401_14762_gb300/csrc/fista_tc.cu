@@ -36,6 +36,7 @@ struct FtcParams {
   uint8_t* conv_out;
   int* status;
   const float* beta;  // momentum weights beta_i, i = 1..iters
+  int inject_timeout;  // test hook: the first product is not issued (see launch_fista_tc)
 };
 
 using tc::put_operand8;
@@ -164,7 +165,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_fista_tc(FtcParams p) {
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
-    if (tid == 0) {
+    if (tid == 0 && !(p.inject_timeout && i == 1)) {
       tc::split_product(tR, tc::smem_u32(sO), tc::smem_u32(sAh), tc::smem_u32(sAl), Mp, S,
                         true, id2);
       tc::mma_commit(&mbar);
@@ -282,6 +283,7 @@ cudaError_t launch_fista_tc(const Ctx& c, const ConvexArgs& a) {
   p.conv_out = a.conv_out;
   p.status = c.status;
   p.beta = c.beta;
+  p.inject_timeout = tc::inject_timeout();
   if (a.P == 0) return cudaSuccess;
   // at least 120 KB so that one CTA (which takes all 512 TMEM columns) runs per SM
   size_t smem = tc_smem(p.Mp, p.Np);

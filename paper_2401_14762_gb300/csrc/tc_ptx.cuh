@@ -5,6 +5,7 @@
 
 #include <cuda_bf16.h>
 #include <stdint.h>
+#include <stdlib.h>
 
 namespace cs {
 namespace tc {
@@ -57,6 +58,14 @@ __device__ __forceinline__ uint64_t globaltimer_ns() {
   uint64_t t;
   asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
   return t;
+}
+
+// Fault injection for the tests of the timeout path: with CS_HSI_INJECT_MMA_TIMEOUT=1 in
+// the environment, the tensor-core kernels leave out their first product, so its bounded
+// wait runs out and the call reports CS_ERR_TIMEOUT without hanging or faulting the GPU.
+inline int inject_timeout() {
+  const char* v = getenv("CS_HSI_INJECT_MMA_TIMEOUT");
+  return v && v[0] == '1' && v[1] == 0;
 }
 
 // Waits for the mbarrier phase with the given parity; gives up after limit_ns nanoseconds
