@@ -69,6 +69,7 @@ struct GrParams {
   int start_done;
   int max_iters;
   int cmax, dmax, kmax, selmax;
+  int d32;           // rows of the FP32 factor kept in shared memory (<= dmax)
   int warp_bytes;
   int* status;
   unsigned long long* counter;
@@ -85,7 +86,8 @@ struct Layout {
   int y, rf, r, xd, b, inc, c, q, sel, xq, L, invd, v, s, wv, Lq, invq, vq, sq,
       svals, cx, cq, ring, total;
   __host__ __device__ Layout(int M, int N, int cmax, int dmax, int kmax, int selmax,
-                             bool fp64_smem, bool need_q, bool need_cyc, bool need_xd) {
+                             bool fp64_smem, bool need_q, bool need_cyc, bool need_xd,
+                             int d32) {
     const int fw = fp64_smem ? 8 : 4;
     int o = 0;
     auto take = [&](int bytes, int align) {
@@ -96,8 +98,9 @@ struct Layout {
     };
     b = take(8 * N, 8);
     xq = take(8 * kmax, 8);
-    L = take(fw * (dmax * (dmax + 1) / 2), 8);
-    invd = take(fw * dmax, 8);
+    const int df = fp64_smem ? dmax : d32;  // factor rows held here
+    L = take(fw * (df * (df + 1) / 2), 8);
+    invd = take(fw * df, 8);
     v = take(8 * dmax, 8);
     s = take(8 * cmax, 8);
     wv = take(8 * dmax, 8);
@@ -761,6 +764,13 @@ template <int VR>
 __device__ bool ls_solve_grow(Warp& w, const int16_t* atoms, int& nf, int n, double* Lbuf,
                               double* invdbuf, double* vbuf, double* s, int cap) {
   fill_rhs(w, atoms, n, vbuf);
+  if (n > w.p.d32 && w.fb) {
+    // the support outgrew the shared-memory factor: FP64 in the warp's global slot
+    nf = 0;
+    const int D = w.p.dmax;
+    double* Lg = w.fb;
+    return ls_fresh(w, atoms, n, Lg, Lg + D * (D + 1) / 2, Lg + D * (D + 1) / 2 + D, s, D);
+  }
   float* L32 = reinterpret_cast<float*>(Lbuf);
   float* inv32 = reinterpret_cast<float*>(invdbuf);
   const bool factored = chol32_append<VR>(w, L32, inv32, nf, n, atoms);
@@ -843,7 +853,7 @@ __global__ void __launch_bounds__(256, 2) k_greedy(GrParams p) {
   extern __shared__ __align__(16) unsigned char gsm[];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   Layout lay(p.Mmax, p.Nmax, p.cmax, p.dmax, p.kmax, p.selmax, p.fb64 == nullptr,
-             ALGO == kGomp, ALGO != kGomp, ALGO == kBiht);
+             ALGO == kGomp, ALGO != kGomp, ALGO == kBiht, p.d32);
   unsigned char* base = gsm + (size_t)wid * p.warp_bytes;
   Warp w{p, lane, p.cubes};
   w.y = (double*)(base + lay.y);
@@ -1304,6 +1314,7 @@ void capacities(GrParams& p, GreedyAlgo algo, const GreedyArgs& a, int Mmax, int
   if (cmax < 1) cmax = 1;
   p.cmax = cmax;
   p.dmax = cmax < Mmax ? cmax : Mmax;
+  p.d32 = p.dmax;
   p.kmax = K > 0 ? K : 1;
   int sel = p.kmax;
   if (algo == kCosamp) sel = 2 * p.kmax;
@@ -1354,8 +1365,21 @@ cudaError_t run_greedy(Ctx& c, GreedyAlgo algo, const GreedyArgs& a, const GrCub
   capacities(p, algo, a, Mmax, Nmax);
   // FP32 factors in shared memory; the rare FP64 fallback (and the |c| > M minimum-norm
   // solve) use one global slot per resident warp, so more warps fit on an SM.
+  if (algo == kGomp) {
+    // gOMP's support grows by G atoms per iteration up to dmax, but its residual usually
+    // stops changing before the support reaches twice kappa: the FP32 factor in shared
+    // memory holds at most 64 rows (two register slots per lane), fewer if that seats 16
+    // warps per SM, but never fewer than 2 kappa; a support that outgrows it is solved by
+    // the FP64 factorisation in the warp's global slot.
+    const int lo = 2 * p.kmax < p.dmax ? 2 * p.kmax : p.dmax;
+    int d = p.dmax < 64 ? p.dmax : 64;
+    while (d > lo && Layout(Mmax, Nmax, p.cmax, p.dmax, p.kmax, p.selmax, false, true, false,
+                            false, d).total * 8 > 110 * 1024)
+      --d;
+    p.d32 = d > lo ? d : lo;
+  }
   Layout lay(Mmax, Nmax, p.cmax, p.dmax, p.kmax, p.selmax, false, algo == kGomp,
-             algo != kGomp, algo == kBiht);
+             algo != kGomp, algo == kBiht, p.d32);
   p.warp_bytes = lay.total;
   // one CTA of up to 8 warps per SM, or two smaller ones if that seats more warps
   int warps1 = (220 * 1024) / lay.total, warps2 = (110 * 1024) / lay.total;
@@ -1391,7 +1415,9 @@ cudaError_t run_greedy(Ctx& c, GreedyAlgo algo, const GreedyArgs& a, const GrCub
     kern<<<(unsigned)grid, warps * 32, smem, c.stream>>>(p);
     return cudaGetLastError();
   };
-  const int vr = (p.dmax + 31) / 32;
+  // register slots of the FP32 factor: rows up to d32 (gOMP's refit on q: up to kmax)
+  const int rows = p.d32 > p.kmax ? p.d32 : p.kmax;
+  const int vr = ((rows < p.dmax ? rows : p.dmax) + 31) / 32;
   if (algo == kGomp) return launch(greedy_kernel<kGomp>(vr));
   if (algo == kBiht) return launch(greedy_kernel<kBiht>(vr));
   return launch(greedy_kernel<kCosamp>(vr));
@@ -1561,7 +1587,7 @@ cudaError_t launch_gomp_noalloc(const double* A64, int M, int N, const GreedyArg
   p.status = reinterpret_cast<int*>(s + lay.status);
   p.counter = reinterpret_cast<unsigned long long*>(s + lay.counter);
   capacities(p, kGomp, a, M, N);
-  Layout wl(M, N, p.cmax, p.dmax, p.kmax, p.selmax, true, true, false, false);
+  Layout wl(M, N, p.cmax, p.dmax, p.kmax, p.selmax, true, true, false, false, p.dmax);
   p.warp_bytes = wl.total;
   int warps = (220 * 1024) / wl.total;
   if (warps > 8) warps = 8;

@@ -165,6 +165,19 @@ def test_gomp_powerlaw(cs, plaw):
     exact_check(Xg, it, Xo, ito, 20)
 
 
+def test_gomp_support_outgrows_shared_factor(cs, plaw):
+    """gOMP keeps at most 64 rows of its FP32 factor in shared memory (fewer if that seats
+    16 warps per SM, never fewer than 2 kappa): 59 rows at M = 80, N = 200, kappa = G = 9.
+    Supports of 63 and 72 atoms (7 and 8 iterations) outgrow it, and those solves move to
+    the FP64 factorisation in the warp's global slot: every pixel still follows the
+    oracle's trajectory."""
+    Xo, ito, _ = orc.gomp(plaw.A, plaw.Y, 9, 9)
+    assert (9 * ito > 59).sum() >= 5  # pixels that overflow
+    ctx = cs.cs_create(plaw.M, plaw.N, Phi=plaw.Phi)
+    Xg, it, _ = gpu_run(cs.cs_recover_gomp, ctx, plaw.Y, plaw.N, 9, 9)
+    exact_check(Xg, it, Xo, ito, 9)
+
+
 def test_gomp_is_omp_exact(cs):
     """gOMP with G = 1 on [I | H/8]: OMP recovers every 4-sparse x exactly."""
     import scipy.linalg
