@@ -76,6 +76,11 @@ def _configure(lib):
                                 i32]
         lib.or_cosamp.argtypes = [i32, i32, _dp, i64, _dp, _dp, i32, dbl, i32, _ip, _dp, i32]
         lib.or_sparsify.argtypes = [i32, _dp, i64, _dp, dbl, i32, _dp, _ip]
+        lib.or_dft_psi.argtypes = [i32, _dp]
+        lib.or_partial_fourier.argtypes = [i32, i32, _ip, _dp]
+        lib.or_cfista.argtypes = [i32, i32, _dp, i64, _dp, _dp, dbl, dbl, dbl, i32, _ip, i32]
+        lib.or_cgomp.argtypes = [i32, i32, _dp, i64, _dp, _dp, i32, i32, dbl, i32, _ip, i32]
+        lib.or_ccosamp.argtypes = [i32, i32, _dp, i64, _dp, _dp, i32, dbl, i32, _ip, i32]
         lib.or_max_threads.restype = i32
         _lib = lib
     return _lib
@@ -249,6 +254,72 @@ def sparsify(F, T, ddof=1, Psi=None):
     if rc:
         raise ValueError(f"or_sparsify failed ({rc})")
     return X, kappa
+
+
+# --------------------------------------------------------------------------
+# Section II with the paper's complex transform: unitary DFT Psi, Phi keeping M rows
+# (partial Fourier).  Complex arrays are numpy complex128 (interleaved doubles).
+# --------------------------------------------------------------------------
+def _c128(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.complex128)
+
+
+def dft_psi(N: int) -> np.ndarray:
+    """Unitary DFT synthesis matrix: Psi[n][k] = exp(-2 pi i n k / N) / sqrt(N)."""
+    out = np.empty((N, N), dtype=np.complex128)
+    _load().or_dft_psi(N, _ptr(out))
+    return out
+
+
+def partial_fourier(M: int, N: int, rows) -> np.ndarray:
+    """A = Phi Psi with Phi keeping the spectral samples `rows` (M distinct indices)."""
+    rows = np.ascontiguousarray(rows, dtype=np.int32)
+    A = np.empty((M, N), dtype=np.complex128)
+    rc = _load().or_partial_fourier(M, N, _iptr(rows), _ptr(A))
+    if rc:
+        raise ValueError(f"or_partial_fourier failed ({rc})")
+    return A
+
+
+def _cprep(A, Y):
+    A, Y = _c128(A), _c128(np.atleast_2d(Y))
+    return A, Y, A.shape[0], A.shape[1], Y.shape[0]
+
+
+def cfista(A, Y, L, lam, eps=0.0, max_iters=500, threads=0):
+    """Algorithm 1 on complex data (modulus soft threshold).  Returns (X, iterations)."""
+    A, Y, M, N, P = _cprep(A, Y)
+    X = np.zeros((P, N), dtype=np.complex128)
+    it = np.zeros(P, dtype=np.int32)
+    rc = _load().or_cfista(M, N, _ptr(A), P, _ptr(Y), _ptr(X), float(L), float(lam), float(eps),
+                           int(max_iters), _iptr(it), int(threads))
+    if rc:
+        raise ValueError(f"or_cfista failed ({rc})")
+    return X, it
+
+
+def cgomp(A, Y, kappa, G, eps=1e-8, max_iters=1 << 30, threads=0):
+    """Algorithm 3 on complex data.  Returns (X, iterations)."""
+    A, Y, M, N, P = _cprep(A, Y)
+    X = np.zeros((P, N), dtype=np.complex128)
+    it = np.zeros(P, dtype=np.int32)
+    rc = _load().or_cgomp(M, N, _ptr(A), P, _ptr(Y), _ptr(X), int(kappa), int(G), float(eps),
+                          int(max_iters), _iptr(it), int(threads))
+    if rc:
+        raise ValueError(f"or_cgomp failed ({rc})")
+    return X, it
+
+
+def ccosamp(A, Y, kappa, eps=1e-8, max_iters=100, threads=0):
+    """Algorithm 5 on complex data.  Returns (X, iterations)."""
+    A, Y, M, N, P = _cprep(A, Y)
+    X = np.zeros((P, N), dtype=np.complex128)
+    it = np.zeros(P, dtype=np.int32)
+    rc = _load().or_ccosamp(M, N, _ptr(A), P, _ptr(Y), _ptr(X), int(kappa), float(eps),
+                            int(max_iters), _iptr(it), int(threads))
+    if rc:
+        raise ValueError(f"or_ccosamp failed ({rc})")
+    return X, it
 
 
 # --------------------------------------------------------------------------

@@ -31,6 +31,13 @@
  *   R8  The loop runs while Delta >= eps and fewer than max_iters iterations ran;
  *       eps = 0 gives a fixed iteration count.  The time cap t_conv is not used.
  *   R9  ADMM returns the x iterate of Algorithm 2 (the variable its residual uses).
+ *   R11 The paper's own transform (Section II): Psi is the unitary DFT, Psi[n][k] =
+ *       exp(-2 pi i n k / N) / sqrt(N) (f in the DFT domain, x = Psi^H f in the IDFT
+ *       domain), Phi keeps M of the N spectral samples (rows), so A = Psi(rows, :) and
+ *       y, x, f are complex.  FISTA thresholds the modulus (x_k scaled by
+ *       max(|a_k| - t, 0) / |a_k|, 0 at a_k = 0); the greedy selections rank |A^H r| and
+ *       |s|; least squares by complex Householder QR (full column rank required);
+ *       A^* is the conjugate transpose.
  *   R10 Sparsification (Section II): x = Psi^T f (Psi orthonormal, so Psi^T = Psi^{-1});
  *       mu and sigma are the mean and the standard deviation of |x| over the N
  *       coefficients, sigma normalised by N - ddof (ddof = 1: sample form, the default;
@@ -39,6 +46,7 @@
  *
  * Layout: all matrices row-major. A is M x N, X is P x N, Y is P x M.
  */
+#include <complex.h>
 #include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
@@ -759,6 +767,308 @@ int or_cosamp(int M, int N, const double *A, int64_t P, const double *Y, double 
     if (!bad) ws_free(&w);
   }
   return OR_OK;
+}
+
+/* ------------------------------------------------------------------------- */
+/* The paper's complex setup (Section II, reading R11): unitary DFT Psi,      */
+/* Phi keeping M rows.  Complex arrays are interleaved (re, im) doubles.      */
+/* ------------------------------------------------------------------------- */
+typedef double complex cplx;
+
+/* Psi[n][k] = exp(-2 pi i n k / N) / sqrt(N) */
+void or_dft_psi(int N, cplx *Psi) {
+  const double pi = 3.14159265358979323846;
+  for (int n = 0; n < N; ++n)
+    for (int k = 0; k < N; ++k) {
+      /* n k mod N keeps the angle exact for large products */
+      const double ang = -2.0 * pi * (double)(((long long)n * k) % N) / N;
+      Psi[(size_t)n * N + k] = (cos(ang) + sin(ang) * _Complex_I) / sqrt((double)N);
+    }
+}
+
+/* A = Phi Psi with Phi keeping the rows rows[0..M): A[m][k] = Psi[rows[m]][k] */
+int or_partial_fourier(int M, int N, const int *rows, cplx *A) {
+  if (M <= 0 || N <= 0 || M > N) return OR_ERR_ARG;
+  cplx *Psi = (cplx *)malloc(sizeof(cplx) * N * N);
+  if (!Psi) return OR_ERR_NOMEM;
+  or_dft_psi(N, Psi);
+  for (int m = 0; m < M; ++m) {
+    if (rows[m] < 0 || rows[m] >= N) {
+      free(Psi);
+      return OR_ERR_ARG;
+    }
+    for (int k = 0; k < N; ++k) A[(size_t)m * N + k] = Psi[(size_t)rows[m] * N + k];
+  }
+  free(Psi);
+  return OR_OK;
+}
+
+/* out = A v */
+static void cmat_vec(int M, int N, const cplx *A, const cplx *v, cplx *out) {
+  for (int m = 0; m < M; ++m) {
+    cplx s = 0.0;
+    for (int n = 0; n < N; ++n) s += A[(size_t)m * N + n] * v[n];
+    out[m] = s;
+  }
+}
+
+/* out = A^H v (conjugate transpose) */
+static void cmat_h_vec(int M, int N, const cplx *A, const cplx *v, cplx *out) {
+  for (int n = 0; n < N; ++n) {
+    cplx s = 0.0;
+    for (int m = 0; m < M; ++m) s += conj(A[(size_t)m * N + n]) * v[m];
+    out[n] = s;
+  }
+}
+
+/* complex soft threshold: a scaled by max(|a| - t, 0) / |a| (0 at a = 0) */
+static cplx csoft(cplx a, double t) {
+  const double mag = cabs(a);
+  if (!(mag > t)) return 0.0;
+  return a * ((mag - t) / mag);
+}
+
+/* r = y - A x, returns ||r - r_prev|| and moves r into r_prev */
+static double cresidual_delta(int M, int N, const cplx *A, const cplx *y, const cplx *x, cplx *r,
+                              cplx *r_prev) {
+  cmat_vec(M, N, A, x, r);
+  double d = 0.0;
+  for (int m = 0; m < M; ++m) {
+    r[m] = y[m] - r[m];
+    const cplx e = r[m] - r_prev[m];
+    d += creal(e) * creal(e) + cimag(e) * cimag(e);
+    r_prev[m] = r[m];
+  }
+  return sqrt(d);
+}
+
+/* FISTA (Algorithm 1) on complex data: the steps of or_fista with A^H and csoft. */
+int or_cfista(int M, int N, const cplx *A, int64_t P, const cplx *Y, cplx *X, double L,
+              double lambda, double eps, int max_iters, int32_t *iters_out, int n_threads) {
+  if (M <= 0 || N <= 0 || P < 0 || !(L > 0.0) || lambda < 0.0 || max_iters < 0)
+    return OR_ERR_ARG;
+  set_threads(n_threads);
+#pragma omp parallel
+  {
+    cplx *buf = (cplx *)malloc(sizeof(cplx) * (5 * N + 3 * M));
+    cplx *x = buf, *x_prev = x + N, *z = x_prev + N, *aux = z + N, *g = aux + N;
+    cplx *v = g + N, *r = v + M, *r_prev = r + M;
+#pragma omp for schedule(dynamic, 16)
+    for (int64_t p = 0; p < P; ++p) {
+      const cplx *y = Y + p * M;
+      for (int n = 0; n < N; ++n) x[n] = z[n] = 0.0;
+      memcpy(r_prev, y, sizeof(cplx) * M);
+      double t = 1.0, delta = 1.0;
+      int it = 0;
+      while (delta >= eps && it < max_iters) {
+        /* 1. aux = z - (1/L) A^H (A z - y) */
+        cmat_vec(M, N, A, z, v);
+        for (int m = 0; m < M; ++m) v[m] -= y[m];
+        cmat_h_vec(M, N, A, v, g);
+        for (int n = 0; n < N; ++n) aux[n] = z[n] - (g[n] / L);
+        /* 2. x = modulus soft threshold of aux at lambda / L */
+        memcpy(x_prev, x, sizeof(cplx) * N);
+        const double thr = lambda / L;
+        for (int n = 0; n < N; ++n) x[n] = csoft(aux[n], thr);
+        /* 3-4. momentum */
+        const double tn = (1.0 + sqrt(4.0 * t * t + 1.0)) / 2.0;
+        for (int n = 0; n < N; ++n) z[n] = x[n] + ((t - 1.0) / tn) * (x[n] - x_prev[n]);
+        t = tn;
+        /* 5. r = y - A x, Delta */
+        delta = cresidual_delta(M, N, A, y, x, r, r_prev);
+        ++it;
+      }
+      memcpy(X + p * N, x, sizeof(cplx) * N);
+      if (iters_out) iters_out[p] = it;
+    }
+    free(buf);
+  }
+  return OR_OK;
+}
+
+/* s = B^+ y for B = A(:, c) of full column rank (nc <= M), by complex Householder QR:
+ * column j is reflected onto alpha e_j with alpha = -e^{i arg(x_0)} ||x||.  Returns 1 if
+ * a column is (numerically) dependent on the earlier ones. */
+static int cqr_lstsq(int M, int N, const cplx *A, const int *c, int nc, const cplx *y, cplx *s,
+                     cplx *work) {
+  if (nc > M) return 1;
+  cplx *B = work, *b = B + (size_t)M * nc, *v = b + M;
+  for (int m = 0; m < M; ++m) {
+    for (int j = 0; j < nc; ++j) B[(size_t)m * nc + j] = A[(size_t)m * N + c[j]];
+    b[m] = y[m];
+  }
+  double scale = 0.0;
+  for (int m = 0; m < M; ++m)
+    for (int j = 0; j < nc; ++j) scale = fmax(scale, cabs(B[(size_t)m * nc + j]));
+  for (int j = 0; j < nc; ++j) {
+    double nrm2 = 0.0;
+    for (int m = j; m < M; ++m) nrm2 += creal(B[(size_t)m * nc + j] * conj(B[(size_t)m * nc + j]));
+    const double nrm = sqrt(nrm2);
+    if (!(nrm > 1e-13 * scale * sqrt((double)M))) return 1;
+    const cplx x0 = B[(size_t)j * nc + j];
+    const cplx phase = cabs(x0) > 0.0 ? x0 / cabs(x0) : 1.0;
+    const cplx alpha = -phase * nrm;
+    double vn2 = 0.0;
+    for (int m = j; m < M; ++m) {
+      v[m] = B[(size_t)m * nc + j] - (m == j ? alpha : 0.0);
+      vn2 += creal(v[m] * conj(v[m]));
+    }
+    /* H = I - 2 v v^H / (v^H v) applied to the remaining columns and to b */
+    for (int k = j; k < nc; ++k) {
+      cplx d = 0.0;
+      for (int m = j; m < M; ++m) d += conj(v[m]) * B[(size_t)m * nc + k];
+      d = 2.0 * d / vn2;
+      for (int m = j; m < M; ++m) B[(size_t)m * nc + k] -= d * v[m];
+    }
+    cplx d = 0.0;
+    for (int m = j; m < M; ++m) d += conj(v[m]) * b[m];
+    d = 2.0 * d / vn2;
+    for (int m = j; m < M; ++m) b[m] -= d * v[m];
+  }
+  /* R s = (Q^H y)[0..nc) */
+  for (int j = nc - 1; j >= 0; --j) {
+    cplx acc = b[j];
+    for (int k = j + 1; k < nc; ++k) acc -= B[(size_t)j * nc + k] * s[k];
+    s[j] = acc / B[(size_t)j * nc + j];
+  }
+  return 0;
+}
+
+typedef struct {
+  cplx *x, *p, *s, *r, *r_prev, *lsw;
+  double *mag;
+  int *c, *theta, *q, *cand;
+  unsigned char *taken, *in_c;
+} cgreedy_ws;
+
+static int cws_alloc(cgreedy_ws *w, int M, int N) {
+  const size_t lsw = (size_t)M * N + 2 * (size_t)M + 16;
+  w->x = (cplx *)malloc(sizeof(cplx) * (3 * (size_t)N + 2 * (size_t)M + lsw));
+  w->mag = (double *)malloc(sizeof(double) * N);
+  w->c = (int *)malloc(sizeof(int) * 4 * N);
+  w->taken = (unsigned char *)malloc(2 * N);
+  if (!w->x || !w->mag || !w->c || !w->taken) return 1;
+  w->p = w->x + N;
+  w->s = w->p + N;
+  w->r = w->s + N;
+  w->r_prev = w->r + M;
+  w->lsw = w->r_prev + M;
+  w->theta = w->c + N;
+  w->q = w->theta + N;
+  w->cand = w->q + N;
+  w->in_c = w->taken + N;
+  return 0;
+}
+
+static void cws_free(cgreedy_ws *w) {
+  free(w->x);
+  free(w->mag);
+  free(w->c);
+  free(w->taken);
+}
+
+/* gOMP (Algorithm 3) on complex data: Theta = the G largest |A^H r|, c = Theta U c,
+ * s = B^+ y, q = the kappa largest |s| over c, refit on q, r = y - A x, Delta (R4, R5). */
+int or_cgomp(int M, int N, const cplx *A, int64_t P, const cplx *Y, cplx *X, int kappa, int G,
+             double eps, int max_iters, int32_t *iters_out, int n_threads) {
+  if (M <= 0 || N <= 0 || P < 0 || kappa < 0 || kappa > N || G < 1 || G > N || max_iters < 0)
+    return OR_ERR_ARG;
+  int cap = max_iters;
+  if (kappa < cap) cap = kappa;
+  if (cap > M / G) cap = M / G;
+  int fail = 0;
+  set_threads(n_threads);
+#pragma omp parallel reduction(| : fail)
+  {
+    cgreedy_ws cw;
+    int bad = cws_alloc(&cw, M, N);
+    fail |= bad;
+#pragma omp for schedule(dynamic, 4)
+    for (int64_t p = 0; p < P; ++p) {
+      if (bad) continue;
+      const cplx *y = Y + p * M;
+      for (int n = 0; n < N; ++n) cw.x[n] = 0.0;
+      memcpy(cw.r_prev, y, sizeof(cplx) * M);
+      int nc = 0;
+      for (int n = 0; n < N; ++n) cw.cand[n] = n;
+      double delta = 1.0;
+      int it = 0;
+      while (delta >= eps && it < cap) {
+        cmat_h_vec(M, N, A, cw.r_prev, cw.p);
+        for (int n = 0; n < N; ++n) cw.mag[n] = cabs(cw.p[n]);
+        argmax_k(cw.mag, cw.cand, N, G, cw.theta, cw.taken);
+        nc = support_union(N, cw.c, nc, cw.theta, G, cw.in_c);
+        fail |= cqr_lstsq(M, N, A, cw.c, nc, y, cw.s, cw.lsw);
+        for (int n = 0; n < N; ++n) cw.mag[n] = 0.0;
+        for (int j = 0; j < nc; ++j) cw.mag[cw.c[j]] = cabs(cw.s[j]);
+        const int nq = nc < kappa ? nc : kappa;
+        if (nc > kappa) argmax_k(cw.mag, cw.c, nc, kappa, cw.q, cw.taken);
+        else
+          for (int j = 0; j < nc; ++j) cw.q[j] = cw.c[j];
+        fail |= cqr_lstsq(M, N, A, cw.q, nq, y, cw.s, cw.lsw);
+        for (int n = 0; n < N; ++n) cw.x[n] = 0.0;
+        for (int j = 0; j < nq; ++j) cw.x[cw.q[j]] = cw.s[j];
+        delta = cresidual_delta(M, N, A, y, cw.x, cw.r, cw.r_prev);
+        ++it;
+      }
+      memcpy(X + p * N, cw.x, sizeof(cplx) * N);
+      if (iters_out) iters_out[p] = it;
+    }
+    if (!bad) cws_free(&cw);
+  }
+  return fail ? OR_ERR_ARG : OR_OK;
+}
+
+/* CoSaMP (Algorithm 5) on complex data: Theta = the 2 kappa largest |A^H r|, c = Theta U c,
+ * s = B^+ y, keep the kappa largest |s| (c = c(q), x(c) = s(q)), r = y - A x, Delta. */
+int or_ccosamp(int M, int N, const cplx *A, int64_t P, const cplx *Y, cplx *X, int kappa,
+               double eps, int max_iters, int32_t *iters_out, int n_threads) {
+  if (M <= 0 || N <= 0 || P < 0 || kappa < 0 || 2 * kappa > N || max_iters < 0)
+    return OR_ERR_ARG;
+  int fail = 0;
+  set_threads(n_threads);
+#pragma omp parallel reduction(| : fail)
+  {
+    cgreedy_ws cw;
+    int bad = cws_alloc(&cw, M, N);
+    fail |= bad;
+#pragma omp for schedule(dynamic, 4)
+    for (int64_t p = 0; p < P; ++p) {
+      if (bad) continue;
+      const cplx *y = Y + p * M;
+      for (int n = 0; n < N; ++n) cw.x[n] = 0.0;
+      memcpy(cw.r_prev, y, sizeof(cplx) * M);
+      int nc = 0;
+      for (int n = 0; n < N; ++n) cw.cand[n] = n;
+      double delta = 1.0;
+      int it = 0;
+      while (delta >= eps && it < max_iters) {
+        cmat_h_vec(M, N, A, cw.r_prev, cw.p);
+        for (int n = 0; n < N; ++n) cw.mag[n] = cabs(cw.p[n]);
+        argmax_k(cw.mag, cw.cand, N, 2 * kappa, cw.theta, cw.taken);
+        nc = support_union(N, cw.c, nc, cw.theta, 2 * kappa, cw.in_c);
+        fail |= cqr_lstsq(M, N, A, cw.c, nc, y, cw.s, cw.lsw);
+        for (int n = 0; n < N; ++n) cw.mag[n] = 0.0;
+        for (int j = 0; j < nc; ++j) cw.mag[cw.c[j]] = cabs(cw.s[j]);
+        const int nq = nc < kappa ? nc : kappa;
+        if (nc > kappa) argmax_k(cw.mag, cw.c, nc, kappa, cw.q, cw.taken);
+        else
+          for (int j = 0; j < nc; ++j) cw.q[j] = cw.c[j];
+        /* x(q) = s(q), c = q (s is indexed by position in c) */
+        for (int n = 0; n < N; ++n) cw.x[n] = 0.0;
+        for (int j = 0; j < nc; ++j) cw.p[cw.c[j]] = cw.s[j];
+        for (int j = 0; j < nq; ++j) cw.x[cw.q[j]] = cw.p[cw.q[j]];
+        for (int j = 0; j < nq; ++j) cw.c[j] = cw.q[j];
+        nc = nq;
+        delta = cresidual_delta(M, N, A, y, cw.x, cw.r, cw.r_prev);
+        ++it;
+      }
+      memcpy(X + p * N, cw.x, sizeof(cplx) * N);
+      if (iters_out) iters_out[p] = it;
+    }
+    if (!bad) cws_free(&cw);
+  }
+  return fail ? OR_ERR_ARG : OR_OK;
 }
 
 int or_max_threads(void) {

@@ -523,4 +523,123 @@ def pin_sparsify_monotone_and_scale_free():
     assert np.array_equal((X0 != 0)[far], (a >= a.mean(axis=1, keepdims=True))[far])
 
 
+# --------------------------------------------------------------------------
+# The paper's complex setup (Section II): unitary DFT Psi, Phi keeping M rows
+# --------------------------------------------------------------------------
+def _rows(M, N, seed):
+    return np.sort(_rng(seed).choice(N, M, replace=False)).astype(np.int32)
+
+
+def _crandn(shape, seed):
+    g = _rng(seed)
+    return g.standard_normal(shape) + 1j * g.standard_normal(shape)
+
+
+def pin_dft_partial_fourier():
+    """Psi is numpy's orthonormal FFT matrix (library routine); the partial-Fourier A has
+    orthonormal rows; A x is the FFT of x at the kept samples."""
+    for N in (8, 120, 200):
+        Psi = orc.dft_psi(N)
+        assert np.abs(Psi - np.fft.fft(np.eye(N), norm="ortho", axis=0)).max() < 1e-12
+        M = (2 * N) // 5
+        rows = _rows(M, N, N)
+        A = orc.partial_fourier(M, N, rows)
+        assert np.abs(A @ A.conj().T - np.eye(M)).max() < 1e-12
+        x = _crandn(N, N + 1)
+        assert np.abs(A @ x - np.fft.fft(x, norm="ortho")[rows]).max() < 1e-12
+
+
+def _csoft_np(a, t):
+    return np.maximum(np.abs(a) - t, 0.0) * np.exp(1j * np.angle(a))
+
+
+def pin_cfista_closed_forms():
+    """First iterate from zero: x1 = modulus-soft(A^H y / L, lambda / L) (the proximal map
+    of the complex l1 norm).  With the full unitary DFT (M = N, L = 1) the LASSO solution
+    is modulus-soft(Psi^H y, lambda), reached at once."""
+    N, M = 64, 26
+    A = orc.partial_fourier(M, N, _rows(M, N, 5))
+    Y = _crandn((3, M), 6)
+    lam, L = 0.05, 1.0
+    X1, _ = orc.cfista(A, Y, L, lam, 0.0, 1)
+    assert np.abs(X1 - _csoft_np(Y @ A.conj() / L, lam / L)).max() < 1e-12
+    Psi = orc.dft_psi(N)
+    Yf = _crandn((3, N), 7)
+    Xf, _ = orc.cfista(Psi, Yf, 1.0, lam, 0.0, 40)
+    assert np.abs(Xf - _csoft_np(np.fft.ifft(Yf, norm="ortho", axis=1), lam)).max() < 1e-12
+
+
+def pin_cfista_kkt():
+    """At convergence the complex LASSO optimality conditions hold: g = A^H (y - A x)
+    equals lambda x_k / |x_k| on the support and has modulus <= lambda off it."""
+    N, M = 64, 26
+    A = orc.partial_fourier(M, N, _rows(M, N, 8))
+    xt = np.zeros((2, N), dtype=complex)
+    xt[:, [3, 17, 40]] = _crandn((2, 3), 9)
+    Y = xt @ A.T + 0.01 * _crandn((2, M), 10)
+    lam = 0.02
+    X, _ = orc.cfista(A, Y, 1.0, lam, 0.0, 5000)
+    for x, y in zip(X, Y):
+        g = A.conj().T @ (y - A @ x)
+        on = np.abs(x) > 1e-9
+        assert on.sum() >= 2
+        assert np.abs(g[on] - lam * x[on] / np.abs(x[on])).max() < 1e-7
+        assert np.abs(g[~on]).max() <= lam * (1 + 1e-7)
+
+
+def pin_complex_reduces_to_real():
+    """On real data the complex routines take every step the real ones take: equal
+    results and iteration counts to those of the (independently pinned) real oracle."""
+    A = sy.gaussian_phi(20, 40, 11)
+    Y = sy.sparse_coeffs(5, 40, 4, 11, "separated") @ A.T + 0.01 * _rng(11).standard_normal(
+        (5, 20))
+    L = orc.lipschitz(A)
+    Xr = orc.fista(A, Y, L, 1e-2, 0.0, 150)[0]
+    Xc, _ = orc.cfista(A, Y, L, 1e-2, 0.0, 150)
+    assert np.abs(Xc - Xr).max() < 1e-10 and np.abs(Xc.imag).max() == 0.0
+    Xr, itr, _ = orc.gomp(A, Y, 6, 2)
+    Xc, itc = orc.cgomp(A, Y, 6, 2)
+    assert np.array_equal(itr, itc) and np.abs(Xc - Xr).max() < 1e-10
+    Xr, itr, _ = orc.cosamp(A, Y, 5)
+    Xc, itc = orc.ccosamp(A, Y, 5)
+    assert np.array_equal(itr, itc) and np.abs(Xc - Xr).max() < 1e-10
+
+
+def pin_cgomp_is_complex_omp():
+    """gOMP with G = 1 is orthogonal matching pursuit: a textbook complex OMP with numpy's
+    least squares gives the same iterates."""
+    N, M, k = 64, 26, 5
+    A = orc.partial_fourier(M, N, _rows(M, N, 12))
+    Y = _crandn((4, M), 13)
+    X, _ = orc.cgomp(A, Y, k, 1, eps=0.0)
+    for x, y in zip(X, Y):
+        r, sup = y.copy(), []
+        for _ in range(k):
+            corr = np.abs(A.conj().T @ r)
+            corr[sup] = -1.0
+            sup.append(int(np.argmax(corr)))
+            s, *_ = np.linalg.lstsq(A[:, sup], y, rcond=None)
+            ref = np.zeros(N, dtype=complex)
+            ref[sup] = s
+            r = y - A @ ref
+        assert np.abs(x - ref).max() < 1e-10
+
+
+def pin_complex_exact_recovery():
+    """Noiseless S-sparse complex pixels measured at 2.5x by a partial Fourier matrix
+    are recovered exactly by gOMP and CoSaMP."""
+    N, M, S = 120, 48, 4
+    A = orc.partial_fourier(M, N, _rows(M, N, 14))
+    Xt = np.zeros((6, N), dtype=complex)
+    g = _rng(15)
+    for i in range(6):
+        Xt[i, g.choice(N, S, replace=False)] = (1.0 + g.random(S)) * np.exp(
+            2j * np.pi * g.random(S))
+    Y = Xt @ A.T
+    Xg, _ = orc.cgomp(A, Y, S, 1)
+    assert np.abs(Xg - Xt).max() < 1e-10
+    Xc, _ = orc.ccosamp(A, Y, S)
+    assert np.abs(Xc - Xt).max() < 1e-10
+
+
 ALL_PINS = [v for k, v in sorted(globals().items()) if k.startswith("pin_")]

@@ -51,6 +51,16 @@ MUTANTS = {
     "sparsify_transposed_psi": ("s += Psi[(size_t)n * N + i] * f[n];",
                                 "s += Psi[(size_t)i * N + n] * f[n];"),
     "sparsify_std_uncentred": ("ss += (a[i] - mu) * (a[i] - mu);", "ss += a[i] * a[i];"),
+    "dft_inverse_sign": ("const double ang = -2.0 * pi", "const double ang = 2.0 * pi"),
+    "complex_no_conjugate": ("s += conj(A[(size_t)m * N + n]) * v[m];",
+                             "s += A[(size_t)m * N + n] * v[m];"),
+    "csoft_real_sign": ("return a * ((mag - t) / mag);",
+                        "return (creal(a) >= 0.0 ? 1.0 : -1.0) * (mag - t);"),
+    "cqr_drops_phase": ("const cplx alpha = -phase * nrm;", "const cplx alpha = -nrm;"),
+    "cgomp_no_refit": ("        fail |= cqr_lstsq(M, N, A, cw.q, nq, y, cw.s, cw.lsw);\n", ""),
+    "ccosamp_selects_kappa": ("argmax_k(cw.mag, cw.cand, N, 2 * kappa, cw.theta, cw.taken);",
+                              "argmax_k(cw.mag, cw.cand, N, kappa, cw.theta, cw.taken);"),
+    "cfista_grad_sign": ("aux[n] = z[n] - (g[n] / L);", "aux[n] = z[n] + (g[n] / L);"),
 }
 
 _RUNNER = r"""
