@@ -81,6 +81,8 @@ def _configure(lib):
         lib.or_cfista.argtypes = [i32, i32, _dp, i64, _dp, _dp, dbl, dbl, dbl, i32, _ip, i32]
         lib.or_cgomp.argtypes = [i32, i32, _dp, i64, _dp, _dp, i32, i32, dbl, i32, _ip, i32]
         lib.or_ccosamp.argtypes = [i32, i32, _dp, i64, _dp, _dp, i32, dbl, i32, _ip, i32]
+        lib.or_cadmm.argtypes = [i32, i32, _dp, i64, _dp, _dp, dbl, dbl, dbl, i32, _ip, i32]
+        lib.or_cbiht.argtypes = [i32, i32, _dp, i64, _dp, _dp, i32, dbl, dbl, i32, _ip, i32]
         lib.or_max_threads.restype = i32
         _lib = lib
     return _lib
@@ -295,6 +297,30 @@ def cfista(A, Y, L, lam, eps=0.0, max_iters=500, threads=0):
                            int(max_iters), _iptr(it), int(threads))
     if rc:
         raise ValueError(f"or_cfista failed ({rc})")
+    return X, it
+
+
+def cadmm(A, Y, rho, lam, eps=0.0, max_iters=500, threads=0):
+    """Algorithm 2 on complex data (threshold lambda / rho).  Returns (X, iterations)."""
+    A, Y, M, N, P = _cprep(A, Y)
+    X = np.zeros((P, N), dtype=np.complex128)
+    it = np.zeros(P, dtype=np.int32)
+    rc = _load().or_cadmm(M, N, _ptr(A), P, _ptr(Y), _ptr(X), float(rho), float(lam), float(eps),
+                          int(max_iters), _iptr(it), int(threads))
+    if rc:
+        raise ValueError(f"or_cadmm failed ({rc})")
+    return X, it
+
+
+def cbiht(A, Y, kappa, mu=0.1, eps=1e-8, max_iters=100, threads=0):
+    """Algorithm 4 on complex data.  Returns (X, iterations)."""
+    A, Y, M, N, P = _cprep(A, Y)
+    X = np.zeros((P, N), dtype=np.complex128)
+    it = np.zeros(P, dtype=np.int32)
+    rc = _load().or_cbiht(M, N, _ptr(A), P, _ptr(Y), _ptr(X), int(kappa), float(mu), float(eps),
+                          int(max_iters), _iptr(it), int(threads))
+    if rc:
+        raise ValueError(f"or_cbiht failed ({rc})")
     return X, it
 
 

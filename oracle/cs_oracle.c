@@ -35,9 +35,9 @@
  *       exp(-2 pi i n k / N) / sqrt(N) (f in the DFT domain, x = Psi^H f in the IDFT
  *       domain), Phi keeps M of the N spectral samples (rows), so A = Psi(rows, :) and
  *       y, x, f are complex.  FISTA thresholds the modulus (x_k scaled by
- *       max(|a_k| - t, 0) / |a_k|, 0 at a_k = 0); the greedy selections rank |A^H r| and
- *       |s|; least squares by complex Householder QR (full column rank required);
- *       A^* is the conjugate transpose.
+ *       max(|a_k| - t, 0) / |a_k|, 0 at a_k = 0), and so does ADMM's z-step; the greedy
+ *       selections rank |A^H r|, |u| and |s|; least squares by complex Householder QR
+ *       (full column rank required); A^* is the conjugate transpose.
  *   R10 Sparsification (Section II): x = Psi^T f (Psi orthonormal, so Psi^T = Psi^{-1});
  *       mu and sigma are the mean and the standard deviation of |x| over the N
  *       coefficients, sigma normalised by N - ddof (ddof = 1: sample form, the default;
@@ -1064,6 +1064,148 @@ int or_ccosamp(int M, int N, const cplx *A, int64_t P, const cplx *Y, cplx *X, i
         ++it;
       }
       memcpy(X + p * N, cw.x, sizeof(cplx) * N);
+      if (iters_out) iters_out[p] = it;
+    }
+    if (!bad) cws_free(&cw);
+  }
+  return fail ? OR_ERR_ARG : OR_OK;
+}
+
+/* In-place Hermitian Cholesky K = L L^H (lower, n x n).  Returns nonzero if K is not
+ * (numerically) positive definite. */
+static int ccholesky(int n, cplx *K) {
+  for (int j = 0; j < n; ++j) {
+    double dj = creal(K[(size_t)j * n + j]);
+    for (int k = 0; k < j; ++k) {
+      const cplx l = K[(size_t)j * n + k];
+      dj -= creal(l) * creal(l) + cimag(l) * cimag(l);
+    }
+    if (!(dj > 0.0)) return 1;
+    dj = sqrt(dj);
+    K[(size_t)j * n + j] = dj;
+    for (int i = j + 1; i < n; ++i) {
+      cplx acc = K[(size_t)i * n + j];
+      for (int k = 0; k < j; ++k) acc -= K[(size_t)i * n + k] * conj(K[(size_t)j * n + k]);
+      K[(size_t)i * n + j] = acc / dj;
+    }
+  }
+  return 0;
+}
+
+/* Solve L L^H v = b in place. */
+static void ccholesky_solve(int n, const cplx *Lf, cplx *b) {
+  for (int i = 0; i < n; ++i) {
+    cplx acc = b[i];
+    for (int k = 0; k < i; ++k) acc -= Lf[(size_t)i * n + k] * b[k];
+    b[i] = acc / Lf[(size_t)i * n + i];
+  }
+  for (int i = n - 1; i >= 0; --i) {
+    cplx acc = b[i];
+    for (int k = i + 1; k < n; ++k) acc -= conj(Lf[(size_t)k * n + i]) * b[k];
+    b[i] = acc / Lf[(size_t)i * n + i];
+  }
+}
+
+/* ADMM (Algorithm 2, reading R1) on complex data: x = (A^H A + alpha I)^{-1}
+ * (A^H y + alpha (z - w)), z = modulus-soft(x + w, lambda / alpha), w += x - z. */
+int or_cadmm(int M, int N, const cplx *A, int64_t P, const cplx *Y, cplx *X, double alpha,
+             double lambda, double eps, int max_iters, int32_t *iters_out, int n_threads) {
+  if (M <= 0 || N <= 0 || P < 0 || !(alpha > 0.0) || lambda < 0.0 || max_iters < 0)
+    return OR_ERR_ARG;
+  cplx *Kc = (cplx *)malloc(sizeof(cplx) * N * N);
+  if (!Kc) return OR_ERR_NOMEM;
+  for (int i = 0; i < N; ++i)
+    for (int j = 0; j < N; ++j) {
+      cplx g = 0.0;
+      for (int m = 0; m < M; ++m) g += conj(A[(size_t)m * N + i]) * A[(size_t)m * N + j];
+      if (i == j) g += alpha;
+      Kc[(size_t)i * N + j] = g;
+    }
+  if (ccholesky(N, Kc)) {
+    free(Kc);
+    return OR_ERR_ARG;
+  }
+  const double zthr = lambda / alpha;
+  set_threads(n_threads);
+#pragma omp parallel
+  {
+    cplx *buf = (cplx *)malloc(sizeof(cplx) * (5 * N + 2 * M));
+    cplx *x = buf, *z = x + N, *wv = z + N, *ahy = wv + N, *rhs = ahy + N;
+    cplx *r = rhs + N, *r_prev = r + M;
+#pragma omp for schedule(dynamic, 16)
+    for (int64_t p = 0; p < P; ++p) {
+      const cplx *y = Y + p * M;
+      for (int n = 0; n < N; ++n) x[n] = z[n] = wv[n] = 0.0;
+      memcpy(r_prev, y, sizeof(cplx) * M);
+      cmat_h_vec(M, N, A, y, ahy);
+      double delta = 1.0;
+      int it = 0;
+      while (delta >= eps && it < max_iters) {
+        for (int n = 0; n < N; ++n) rhs[n] = ahy[n] + alpha * (z[n] - wv[n]);
+        ccholesky_solve(N, Kc, rhs);
+        memcpy(x, rhs, sizeof(cplx) * N);
+        for (int n = 0; n < N; ++n) z[n] = csoft(x[n] + wv[n], zthr);
+        for (int n = 0; n < N; ++n) wv[n] += x[n] - z[n];
+        delta = cresidual_delta(M, N, A, y, x, r, r_prev);
+        ++it;
+      }
+      memcpy(X + p * N, x, sizeof(cplx) * N);
+      if (iters_out) iters_out[p] = it;
+    }
+    free(buf);
+  }
+  free(Kc);
+  return OR_OK;
+}
+
+/* BIHT (Algorithm 4, backtracking IHT) on complex data: u = x_a + mu A^H (y - A x_a),
+ * Theta = the kappa largest |u|, c = supp(x_a) U Theta, s = B^+ y, keep the kappa
+ * largest |s|, r = y - A x, Delta. */
+int or_cbiht(int M, int N, const cplx *A, int64_t P, const cplx *Y, cplx *X, int kappa,
+             double mu, double eps, int max_iters, int32_t *iters_out, int n_threads) {
+  if (M <= 0 || N <= 0 || P < 0 || kappa < 0 || kappa > N || max_iters < 0) return OR_ERR_ARG;
+  int fail = 0;
+  set_threads(n_threads);
+#pragma omp parallel reduction(| : fail)
+  {
+    cgreedy_ws cw;
+    int bad = cws_alloc(&cw, M, N);
+    fail |= bad;
+#pragma omp for schedule(dynamic, 4)
+    for (int64_t p = 0; p < P; ++p) {
+      if (bad) continue;
+      const cplx *y = Y + p * M;
+      cplx *xa = cw.x;
+      for (int n = 0; n < N; ++n) xa[n] = 0.0;
+      memcpy(cw.r_prev, y, sizeof(cplx) * M);
+      for (int n = 0; n < N; ++n) cw.cand[n] = n;
+      double delta = 1.0;
+      int it = 0;
+      while (delta >= eps && it < max_iters) {
+        /* u = x_a + mu A^H (y - A x_a) */
+        cmat_vec(M, N, A, xa, cw.r);
+        for (int m = 0; m < M; ++m) cw.r[m] = y[m] - cw.r[m];
+        cmat_h_vec(M, N, A, cw.r, cw.p);
+        for (int n = 0; n < N; ++n) cw.mag[n] = cabs(xa[n] + mu * cw.p[n]);
+        argmax_k(cw.mag, cw.cand, N, kappa, cw.theta, cw.taken);
+        int nc = 0;
+        for (int n = 0; n < N; ++n)
+          if (cabs(xa[n]) != 0.0) cw.c[nc++] = n;
+        nc = support_union(N, cw.c, nc, cw.theta, kappa, cw.in_c);
+        fail |= cqr_lstsq(M, N, A, cw.c, nc, y, cw.s, cw.lsw);
+        for (int n = 0; n < N; ++n) cw.mag[n] = 0.0;
+        for (int j = 0; j < nc; ++j) cw.mag[cw.c[j]] = cabs(cw.s[j]);
+        const int nh = nc < kappa ? nc : kappa;
+        if (nc > kappa) argmax_k(cw.mag, cw.c, nc, kappa, cw.q, cw.taken);
+        else
+          for (int j = 0; j < nc; ++j) cw.q[j] = cw.c[j];
+        for (int j = 0; j < nc; ++j) cw.p[cw.c[j]] = cw.s[j];
+        for (int n = 0; n < N; ++n) xa[n] = 0.0;
+        for (int j = 0; j < nh; ++j) xa[cw.q[j]] = cw.p[cw.q[j]];
+        delta = cresidual_delta(M, N, A, y, xa, cw.r, cw.r_prev);
+        ++it;
+      }
+      memcpy(X + p * N, xa, sizeof(cplx) * N);
       if (iters_out) iters_out[p] = it;
     }
     if (!bad) cws_free(&cw);

@@ -587,6 +587,22 @@ def pin_cfista_kkt():
         assert np.abs(g[~on]).max() <= lam * (1 + 1e-7)
 
 
+def pin_cadmm_closed_forms():
+    """First iterate from zero: x1 = (A^H A + rho I)^{-1} A^H y = A^H y / (1 + rho) for a
+    partial Fourier A (orthonormal rows, Woodbury).  With the full unitary DFT the
+    fixed point is the LASSO solution modulus-soft(Psi^H y, lambda) (threshold
+    lambda / rho in the z-step, reading R1), here with rho = 2."""
+    N, M = 64, 26
+    A = orc.partial_fourier(M, N, _rows(M, N, 16))
+    Y = _crandn((3, M), 17)
+    X1, _ = orc.cadmm(A, Y, 2.0, 0.05, 0.0, 1)
+    assert np.abs(X1 - (Y @ A.conj()) / 3.0).max() < 1e-12
+    Psi = orc.dft_psi(N)
+    Yf = _crandn((3, N), 18)
+    Xf, _ = orc.cadmm(Psi, Yf, 2.0, 0.05, 0.0, 400)
+    assert np.abs(Xf - _csoft_np(np.fft.ifft(Yf, norm="ortho", axis=1), 0.05)).max() < 1e-10
+
+
 def pin_complex_reduces_to_real():
     """On real data the complex routines take every step the real ones take: equal
     results and iteration counts to those of the (independently pinned) real oracle."""
@@ -603,6 +619,13 @@ def pin_complex_reduces_to_real():
     Xr, itr, _ = orc.cosamp(A, Y, 5)
     Xc, itc = orc.ccosamp(A, Y, 5)
     assert np.array_equal(itr, itc) and np.abs(Xc - Xr).max() < 1e-10
+    Xr = orc.admm(A, Y, 1.5, 1e-2, 0.0, 120)[0]
+    Xc, _ = orc.cadmm(A, Y, 1.5, 1e-2, 0.0, 120)
+    assert np.abs(Xc - Xr).max() < 1e-10
+    for mu in (0.1, 1.0):
+        Xr, itr, _ = orc.biht(A, Y, 5, mu)
+        Xc, itc = orc.cbiht(A, Y, 5, mu)
+        assert np.array_equal(itr, itc) and np.abs(Xc - Xr).max() < 1e-10
 
 
 def pin_cgomp_is_complex_omp():
@@ -627,7 +650,7 @@ def pin_cgomp_is_complex_omp():
 
 def pin_complex_exact_recovery():
     """Noiseless S-sparse complex pixels measured at 2.5x by a partial Fourier matrix
-    are recovered exactly by gOMP and CoSaMP."""
+    are recovered exactly by gOMP, CoSaMP and BIHT with mu = 1."""
     N, M, S = 120, 48, 4
     A = orc.partial_fourier(M, N, _rows(M, N, 14))
     Xt = np.zeros((6, N), dtype=complex)
@@ -640,6 +663,8 @@ def pin_complex_exact_recovery():
     assert np.abs(Xg - Xt).max() < 1e-10
     Xc, _ = orc.ccosamp(A, Y, S)
     assert np.abs(Xc - Xt).max() < 1e-10
+    Xb, _ = orc.cbiht(A, Y, S, 1.0)
+    assert np.abs(Xb - Xt).max() < 1e-10
 
 
 ALL_PINS = [v for k, v in sorted(globals().items()) if k.startswith("pin_")]

@@ -61,6 +61,11 @@ MUTANTS = {
     "ccosamp_selects_kappa": ("argmax_k(cw.mag, cw.cand, N, 2 * kappa, cw.theta, cw.taken);",
                               "argmax_k(cw.mag, cw.cand, N, kappa, cw.theta, cw.taken);"),
     "cfista_grad_sign": ("aux[n] = z[n] - (g[n] / L);", "aux[n] = z[n] + (g[n] / L);"),
+    "ccholesky_no_conjugate": ("acc -= K[(size_t)i * n + k] * conj(K[(size_t)j * n + k]);",
+                               "acc -= K[(size_t)i * n + k] * K[(size_t)j * n + k];"),
+    "cadmm_threshold_times_alpha": ("const double zthr = lambda / alpha;",
+                                    "const double zthr = lambda * alpha;"),
+    "cbiht_step_sign": ("cabs(xa[n] + mu * cw.p[n])", "cabs(xa[n] - mu * cw.p[n])"),
 }
 
 _RUNNER = r"""
