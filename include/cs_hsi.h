@@ -97,6 +97,20 @@ void cs_opts_default(cs_opts *opts);
 cs_status cs_create(cs_ctx **out, int M, int N, const double *A_host, const double *Phi_host,
                     const double *Psi_host, double admm_rho, void *stream);
 
+/* The paper's complex setup (Section II): Psi the unitary DFT and Phi keeping M of the N
+ * spectral samples make A = Phi Psi complex, and x, y complex.  Creates a context for
+ * the complex M x N dictionary A (host, row-major, interleaved (re, im) FP64 pairs:
+ * A[2 (m N + k)] = Re a_mk, A[2 (m N + k) + 1] = Im a_mk) through its real form: a
+ * 2M x 2N real dictionary acting on vectors of (re, im) pairs.  On such a context
+ * cs_measure, cs_recover_fista and cs_recover_admm (also in cs_recover_batch and
+ * cs_recover_stream) take Y as P x 2M and X as P x 2N float32, i.e. complex64 arrays of
+ * P x M and P x N, and FISTA's and ADMM's soft thresholds act on the moduli |x_k|
+ * (x_k scaled by max(|x_k| - t, 0) / |x_k|); L = lambda_max(A^H A).  These run on the
+ * FP32 path (prec is ignored).  The greedy calls and cs_sparsify return CS_ERR_ARG on a
+ * complex context.  Limits: 1 <= M <= N, M <= 64, N <= 128 (CS_ERR_SHAPE). */
+cs_status cs_create_complex(cs_ctx **out, int M, int N, const double *A, double admm_rho,
+                            void *cuda_stream);
+
 /* Releases the context and all device memory it owns. */
 void cs_destroy(cs_ctx *ctx);
 

@@ -22,8 +22,8 @@ CS_FP32, CS_BF16, CS_FP8_E4M3 = 0, 1, 2
 EXPORTED = ["cs_opts_default", "cs_create", "cs_destroy", "cs_get_lipschitz", "cs_get_dictionary",
             "cs_measure", "cs_recover_fista", "cs_recover_admm", "cs_recover_gomp",
             "cs_recover_biht", "cs_recover_cosamp", "cs_get_work", "cs_recover_gomp_noalloc",
-            "cs_recover_batch", "cs_recover_stream", "cs_sparsify", "cs_sync",
-            "cs_last_error"]
+            "cs_recover_batch", "cs_recover_stream", "cs_sparsify", "cs_create_complex",
+            "cs_sync", "cs_last_error"]
 CS_ALGO_FISTA, CS_ALGO_ADMM, CS_ALGO_GOMP, CS_ALGO_BIHT, CS_ALGO_COSAMP = 0, 1, 2, 3, 4
 
 
@@ -69,6 +69,7 @@ def load_library(path: str = LIB_PATH):
     lib.cs_opts_default.restype = None
     lib.cs_create.argtypes = [ctypes.POINTER(vp), i32, i32, vp, vp, vp, dbl, vp]
     lib.cs_destroy.argtypes = [vp]
+    lib.cs_create_complex.argtypes = [ctypes.POINTER(vp), i32, i32, vp, dbl, vp]
     lib.cs_destroy.restype = None
     lib.cs_get_lipschitz.argtypes = [vp, ctypes.POINTER(dbl)]
     lib.cs_get_dictionary.argtypes = [vp, vp]
@@ -191,6 +192,19 @@ def cs_create(M, N, A=None, Phi=None, Psi=None, admm_rho=0.0, stream=None) -> Co
                        float(admm_rho), stream if stream is not None else _default_stream())
     _check(st)
     return Context(h.value, int(M), int(N))
+
+
+def cs_create_complex(M, N, A, admm_rho=0.0, stream=None) -> Context:
+    """Context for the complex M x N dictionary A (the paper's DFT / partial-Fourier
+    setup, Section II).  Y and X on it are complex64 arrays (P x M, P x N) passed as
+    float32 (re, im) pairs; FISTA and ADMM threshold the moduli."""
+    lib = load_library()
+    A = np.ascontiguousarray(np.asarray(A, dtype=np.complex128))
+    h = ctypes.c_void_p()
+    st = lib.cs_create_complex(ctypes.byref(h), int(M), int(N), A.ctypes.data, float(admm_rho),
+                               stream if stream is not None else _default_stream())
+    _check(st)
+    return Context(h.value, 2 * int(M), 2 * int(N))
 
 
 def cs_destroy(ctx: Context):

@@ -254,6 +254,33 @@ cs_status cs_create(cs_ctx** out, int M, int N, const double* A_host, const doub
   return CS_OK;
 }
 
+cs_status cs_create_complex(cs_ctx** out, int M, int N, const double* A_host, double admm_rho,
+                            void* stream) {
+  cs::set_error("");
+  if (!out) return arg_error("out is NULL");
+  *out = nullptr;
+  if (!A_host) return arg_error("A is NULL");
+  if (M < 1 || N < 1 || M > N || 2 * M > cs::kMaxM || 2 * N > cs::kMaxN) {
+    cs::set_error("complex dictionaries need 1 <= M <= N, M <= 64, N <= 128");
+    return CS_ERR_SHAPE;
+  }
+  // the real form of A acting on (re, im) pairs: rows 2m, 2m + 1 and columns 2k, 2k + 1
+  // hold [[Re a, -Im a], [Im a, Re a]] for a = A[m][k]
+  std::vector<double> R((size_t)4 * M * N);
+  const size_t ld = 2 * (size_t)N;
+  for (int m = 0; m < M; ++m)
+    for (int k = 0; k < N; ++k) {
+      const double re = A_host[2 * ((size_t)m * N + k)], im = A_host[2 * ((size_t)m * N + k) + 1];
+      R[(2 * m) * ld + 2 * k] = re;
+      R[(2 * m) * ld + 2 * k + 1] = -im;
+      R[(2 * m + 1) * ld + 2 * k] = im;
+      R[(2 * m + 1) * ld + 2 * k + 1] = re;
+    }
+  cs_status st = cs_create(out, 2 * M, 2 * N, R.data(), nullptr, nullptr, admm_rho, stream);
+  if (st == CS_OK) (*out)->c.complex_pairs = true;
+  return st;
+}
+
 void cs_destroy(cs_ctx* ctx) {
   if (!ctx) return;
   cudaStreamSynchronize(ctx->c.stream);
@@ -389,6 +416,7 @@ static cs_status greedy(cs_ctx* ctx, cs::GreedyAlgo algo, const float* Y, float*
   if (opts) o = *opts;
   if (cs_status s = check_common(ctx, Y, X, P, &o)) return s;
   cs::Ctx& c = ctx->c;
+  if (c.complex_pairs) return arg_error("complex contexts support FISTA and ADMM only");
   int kmax = kappa;
   if (o.kappa_per_pixel) {
     // the caller bounds the per-pixel levels by kappa (used to size the workspace)
@@ -452,6 +480,8 @@ cs_status cs_recover_batch(const cs_batch_item* items, int n_items, cs_algo algo
         (it.converged_out && !cs::is_device_ptr(it.converged_out)) ||
         (it.kappa_per_pixel && !cs::is_device_ptr(it.kappa_per_pixel)))
       return arg_error("per-pixel arrays must be device memory");
+    if (greedy && c.complex_pairs)
+      return arg_error("complex contexts support FISTA and ADMM only");
     if (greedy && it.P > 0) {
       if (kappa < 0 || kappa > c.N) return arg_error("kappa out of range for a cube");
       if (algo == CS_ALGO_COSAMP && 2 * kappa > c.N)
@@ -557,6 +587,7 @@ cs_status cs_recover_stream(cs_ctx* ctx, cs_algo algo, const cs_algo_params* par
   const bool is_greedy = algo >= CS_ALGO_GOMP;
   const int kappa = params->kappa, G = params->G;
   if (is_greedy) {
+    if (c.complex_pairs) return arg_error("complex contexts support FISTA and ADMM only");
     if (kappa < 0 || kappa > c.N) return arg_error("kappa out of range");
     if (algo == CS_ALGO_COSAMP && 2 * kappa > c.N) return arg_error("CoSaMP needs 2 kappa <= N");
     if (algo == CS_ALGO_GOMP && (G < 0 || G > c.N || (G == 0 && !o.kappa_per_pixel)))

@@ -42,6 +42,7 @@ struct CvParams {
   float c1, c2;    // FISTA: 1/L, lambda/L.  ADMM: rho, lambda/rho
   float eps2;      // eps^2 (0 => fixed iteration count)
   int start_done;  // eps > 1: Delta = 1 < eps before the first iteration
+  int pairs;       // complex data as (re, im) pairs: thresholds on the moduli
   int iters;
   int32_t* iters_out;
   uint8_t* conv_out;
@@ -52,6 +53,15 @@ struct CvParams {
 __device__ __forceinline__ float soft_thr(float a, float t) {
   float m = fabsf(a) - t;
   return m > 0.f ? copysignf(m, a) : 0.f;
+}
+
+// The modulus soft threshold of the complex value a0 + i a1: scaled by
+// max(|a| - t, 0) / |a| (0 when |a| <= t).
+__device__ __forceinline__ void soft_pair(float a0, float a1, float t, float& x0, float& x1) {
+  const float m = sqrtf(fmaf(a0, a0, a1 * a1));
+  const float s = m > t ? (m - t) / m : 0.f;
+  x0 = a0 * s;
+  x1 = a1 * s;
 }
 
 __device__ __forceinline__ float f4(const float4& v, int e) {
@@ -204,11 +214,25 @@ __global__ void __launch_bounds__(kThreads, 1) k_fista_f32(CvParams p) {
 #pragma unroll
     for (int i = 0; i < kPPW; ++i) {
       if (done[i]) continue;
+      if (p.pairs) {
+        // a lane's columns 4l..4l+3 hold two whole (re, im) pairs
 #pragma unroll
-      for (int k = 0; k < 4 * NCH; ++k) {
-        float xn = soft_thr(z[i][k] - acc[i][k] * p.c1, p.c2);
-        z[i][k] = xn + beta * (xn - x[i][k]);
-        x[i][k] = xn;
+        for (int k = 0; k < 4 * NCH; k += 2) {
+          float x0, x1;
+          soft_pair(z[i][k] - acc[i][k] * p.c1, z[i][k + 1] - acc[i][k + 1] * p.c1, p.c2, x0,
+                    x1);
+          z[i][k] = x0 + beta * (x0 - x[i][k]);
+          z[i][k + 1] = x1 + beta * (x1 - x[i][k + 1]);
+          x[i][k] = x0;
+          x[i][k + 1] = x1;
+        }
+      } else {
+#pragma unroll
+        for (int k = 0; k < 4 * NCH; ++k) {
+          float xn = soft_thr(z[i][k] - acc[i][k] * p.c1, p.c2);
+          z[i][k] = xn + beta * (xn - x[i][k]);
+          x[i][k] = xn;
+        }
       }
 #pragma unroll
       for (int c = 0; c < NCH; ++c)
@@ -365,12 +389,26 @@ __global__ void __launch_bounds__(kThreads, 1) k_admm_f32(CvParams p) {
     for (int i = 0; i < kPPW; ++i) {
       if (done[i]) continue;
       float x[4 * NCH];
+      if (p.pairs) {
 #pragma unroll
-      for (int k = 0; k < 4 * NCH; ++k) {
-        x[k] = (z[i][k] - w[i][k]) + acc[i][k];
-        float zn = soft_thr(x[k] + w[i][k], thr);
-        w[i][k] = w[i][k] + x[k] - zn;
-        z[i][k] = zn;
+        for (int k = 0; k < 4 * NCH; k += 2) {
+          x[k] = (z[i][k] - w[i][k]) + acc[i][k];
+          x[k + 1] = (z[i][k + 1] - w[i][k + 1]) + acc[i][k + 1];
+          float z0, z1;
+          soft_pair(x[k] + w[i][k], x[k + 1] + w[i][k + 1], thr, z0, z1);
+          w[i][k] = w[i][k] + x[k] - z0;
+          w[i][k + 1] = w[i][k + 1] + x[k + 1] - z1;
+          z[i][k] = z0;
+          z[i][k + 1] = z1;
+        }
+      } else {
+#pragma unroll
+        for (int k = 0; k < 4 * NCH; ++k) {
+          x[k] = (z[i][k] - w[i][k]) + acc[i][k];
+          float zn = soft_thr(x[k] + w[i][k], thr);
+          w[i][k] = w[i][k] + x[k] - zn;
+          z[i][k] = zn;
+        }
       }
       if (fin[i]) {
         done[i] = true;
@@ -470,6 +508,7 @@ CvParams base_params(const Ctx& c) {
   p.A = c.A32;
   p.W = c.W32;
   p.status = c.status;
+  p.pairs = c.complex_pairs ? 1 : 0;
   return p;
 }
 
@@ -533,7 +572,8 @@ cudaError_t launch_fista(Ctx& c, const ConvexArgs& a, bool table) {
     cudaError_t e = momentum_table(c, a.iters);
     if (e != cudaSuccess) return e;
   }
-  if (a.prec != CS_FP32 && fista_tc_supported(c.M, c.N)) return launch_fista_tc(c, a);
+  if (a.prec != CS_FP32 && !c.complex_pairs && fista_tc_supported(c.M, c.N))
+    return launch_fista_tc(c, a);
   CvParams p = base_params(c);
   p.beta = c.beta;
   p.Y = a.Y;
@@ -552,7 +592,8 @@ cudaError_t launch_fista(Ctx& c, const ConvexArgs& a, bool table) {
 }
 
 cudaError_t launch_admm(const Ctx& c, const ConvexArgs& a) {
-  if (a.P > 0 && a.prec != CS_FP32 && admm_tc_supported(c.M, c.N)) return launch_admm_tc(c, a);
+  if (a.P > 0 && a.prec != CS_FP32 && !c.complex_pairs && admm_tc_supported(c.M, c.N))
+    return launch_admm_tc(c, a);
   CvParams p = base_params(c);
   p.Y = a.Y;
   p.X = a.X;

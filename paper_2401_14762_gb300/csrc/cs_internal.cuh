@@ -31,6 +31,9 @@ inline int smem_ld(int n) {
 
 struct Ctx {
   int M = 0, N = 0, device = 0, num_sms = 0;
+  // cs_create_complex: A is the real form of a complex dictionary and every vector holds
+  // complex values as (re, im) pairs; FISTA's and ADMM's thresholds act on the moduli
+  bool complex_pairs = false;
   cudaStream_t stream = nullptr;
   double L = 0.0;             // Lipschitz constant lambda_max(A^T A)
   double* A64 = nullptr;      // M x N, FP64
