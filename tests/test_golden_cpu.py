@@ -24,6 +24,13 @@ def test_oracle_reproduces_stored_results():
     assert abs(got["lipschitz"] - ref["lipschitz"]) <= 1e-12 * ref["lipschitz"]
     for k in ("gomp_iters", "biht_iters", "cosamp_iters", "sparsify_kappa"):
         assert np.array_equal(got[k], np.array(ref[k])), k
+    for k in ("cgomp_iters", "cbiht_iters", "ccosamp_iters"):
+        assert np.array_equal(got[k], np.array(ref[k])), k
+    for k in ("cfista", "cadmm", "cgomp", "cbiht", "ccosamp"):
+        r = np.array(ref[k]["re"]) + 1j * np.array(ref[k]["im"])
+        if k not in ("cfista", "cadmm"):
+            assert np.array_equal(got[k] != 0, r != 0), k
+        assert np.abs(got[k] - r).max() <= 1e-9 * max(1.0, np.abs(r).max()), k
     for k in ("fista", "admm", "gomp", "biht", "cosamp", "sparsify"):
         r = np.array(ref[k])
         if k not in ("fista", "admm"):  # supports and kept sets exactly

@@ -61,3 +61,10 @@ def test_errors_before_any_device_work(lib):
     assert lib.cs_recover_batch(items, 1, 7, ctypes.byref(prm), None) == cs.CS_ERR_ARG
     # sparsification: a NULL context is an argument error
     assert lib.cs_sparsify(None, None, None, 0, 0.1, 1, None, None) == cs.CS_ERR_ARG
+    # complex contexts: shape limits and a NULL dictionary are reported before any device
+    # work (the real form doubles M and N: M <= 64, N <= 128)
+    assert lib.cs_create_complex(ctypes.byref(h), 65, 128, None, 0.0, None) == cs.CS_ERR_ARG
+    A = (ctypes.c_double * (2 * 65 * 130))()
+    assert lib.cs_create_complex(ctypes.byref(h), 65, 130, A, 0.0, None) == cs.CS_ERR_SHAPE
+    assert lib.cs_create_complex(ctypes.byref(h), 8, 4, A, 0.0, None) == cs.CS_ERR_SHAPE
+    assert lib.cs_create_complex(None, 8, 16, A, 0.0, None) == cs.CS_ERR_ARG
