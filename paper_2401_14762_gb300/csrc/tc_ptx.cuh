@@ -116,6 +116,19 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
 #pragma unroll
   for (int j = 0; j < 8; ++j) v[j] = __uint_as_float(r[j]);
 }
+// 16 consecutive FP32 columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+      "%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+#pragma unroll
+  for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+}
 __device__ __forceinline__ void tmem_st8(uint32_t taddr, const float (&v)[8]) {
   asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(
                    taddr),
@@ -197,9 +210,11 @@ __device__ __forceinline__ void split_product(uint32_t d_tmem, uint32_t o, uint3
   }
 }
 
+// sign(a) max(|a| - t, 0) for t >= 0, as a - clamp(a, -t, t): the same value for every
+// finite a (a - t and a + t are the rounded |a| - t with a's sign; |a| <= t gives +0),
+// in three instructions without a compare.
 __device__ __forceinline__ float soft_thr(float a, float t) {
-  float m = fabsf(a) - t;
-  return m > 0.f ? copysignf(m, a) : 0.f;
+  return a - fminf(fmaxf(a, -t), t);
 }
 
 }  // namespace tc

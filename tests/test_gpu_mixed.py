@@ -24,7 +24,8 @@ def cs():
 
 @pytest.mark.parametrize("shape,kind,iters,P", [((80, 200), "powerlaw", 300, 32 * 20 + 7),
                                                 ((48, 120), "powerlaw", 300, 300),
-                                                ((90, 224), "powerlaw", 300, 200)])
+                                                ((90, 224), "powerlaw", 300, 200),
+                                                ((102, 256), "powerlaw", 300, 128 * 3 + 5)])
 def test_fista_bf16_powerlaw(cs, shape, kind, iters, P):
     M, N = shape
     pr = Problem(M, N, P, kind, seed=3, noise_var=1e-3)
