@@ -138,6 +138,20 @@ cs_status check_ctx(const cs_ctx* ctx) {
   return CS_OK;
 }
 
+// The option checks every recovery call makes (context calls and the allocation-free
+// call alike).
+cs_status check_opts(const cs_opts& o) {
+  if (!(o.eps >= 0.0) || !std::isfinite(o.eps)) return arg_error("eps must be >= 0");
+  if (o.max_iters < 0) return arg_error("max_iters < 0");
+  if (o.prec != CS_FP32 && o.prec != CS_BF16 && o.prec != CS_FP8_E4M3)
+    return arg_error("unknown precision");
+  if ((o.iters_out && !is_device_ptr(o.iters_out)) ||
+      (o.converged_out && !is_device_ptr(o.converged_out)) ||
+      (o.kappa_per_pixel && !is_device_ptr(o.kappa_per_pixel)))
+    return arg_error("per-pixel option arrays must be device memory");
+  return CS_OK;
+}
+
 // Runs `fn(Y_dev, X_dev)` on device buffers; host buffers are staged and copied back.
 template <typename F>
 cs_status with_cube(cs_ctx* ctx, const float* Y, float* X, int64_t P, int in_cols, int out_cols,
@@ -361,15 +375,7 @@ static cs_status check_common(const cs_ctx* ctx, const float* Y, float* X, int64
     cs::set_error("P must be below 2^31");
     return CS_ERR_SHAPE;
   }
-  if (!(o->eps >= 0.0) || !std::isfinite(o->eps)) return arg_error("eps must be >= 0");
-  if (o->max_iters < 0) return arg_error("max_iters < 0");
-  if (o->prec != CS_FP32 && o->prec != CS_BF16 && o->prec != CS_FP8_E4M3)
-    return arg_error("unknown precision");
-  if ((o->iters_out && !cs::is_device_ptr(o->iters_out)) ||
-      (o->converged_out && !cs::is_device_ptr(o->converged_out)) ||
-      (o->kappa_per_pixel && !cs::is_device_ptr(o->kappa_per_pixel)))
-    return arg_error("per-pixel option arrays must be device memory");
-  return CS_OK;
+  return cs::check_opts(*o);
 }
 
 cs_status cs_recover_fista(cs_ctx* ctx, const float* Y, float* X, int64_t P, double lambda,
@@ -690,12 +696,7 @@ cs_status cs_recover_gomp_noalloc(const double* A_dev, int M, int N, const float
   if (!cs::is_device_ptr(A_dev) || (P > 0 && (!cs::is_device_ptr(Y) || !cs::is_device_ptr(X))))
     return arg_error("cs_recover_gomp_noalloc takes device memory only (staging host memory "
                      "would allocate)");
-  if (!(o.eps >= 0.0) || !std::isfinite(o.eps)) return arg_error("eps must be >= 0");
-  if (o.max_iters < 0) return arg_error("max_iters < 0");
-  if ((o.iters_out && !cs::is_device_ptr(o.iters_out)) ||
-      (o.converged_out && !cs::is_device_ptr(o.converged_out)) ||
-      (o.kappa_per_pixel && !cs::is_device_ptr(o.kappa_per_pixel)))
-    return arg_error("per-pixel option arrays must be device memory");
+  if (cs_status st = cs::check_opts(o)) return st;
   if (kappa < 0 || kappa > N) return arg_error("kappa out of range");
   if (G < 0 || G > N || (G == 0 && !o.kappa_per_pixel))
     return arg_error("G must be in 1..N (0 only with kappa_per_pixel)");

@@ -4,8 +4,9 @@
 // counter when it finishes, so pixels that stop early (Delta < eps) free their warp at
 // once; a launch may cover several cubes (each with its own dictionary, found through a
 // table of cube descriptors), counted as one run of pixels.  Per iteration the warp
-//   1. correlates: p = A^T r (FP32, lane l owns atoms l, l+32, ...), for BIHT
-//      u = x + mu p,
+//   1. correlates: p = A^T r = A^T y - (A^T A)_{:,q} x_q (FP32, lane l owns atoms l, l+32,
+//      ...; A^T y once per pixel, then |q| <= kappa columns of the Gram matrix instead of
+//      the M rows of A), for BIHT u = x + mu p,
 //   2. selects the G / 2 kappa / kappa largest magnitudes (ties to the lower atom):
 //      warp argmax rounds for small k, a 32-step radix search on the magnitude bits for
 //      large k; the choice is then certified against FP64: atoms whose FP32 value lies
@@ -17,12 +18,18 @@
 //      gathered from the precomputed Gram matrix A^T A, factored in FP32 (gOMP extends
 //      its factor by the rows of the atoms just added instead of refactoring), and the
 //      solution is refined to FP64 accuracy with FP64 residuals (an FP64 factorisation
-//      is the fallback); when |c| > M the minimum-norm solution s = A_c^T (A_c A_c^T)^{-1} y
-//      is used instead,
-//   5. prunes to kappa atoms by rank counting on the FP64 coefficients (and, for gOMP,
-//      refits on them),
-//   6. recomputes the residual r = y - A x and Delta = ||r - r_prev|| in FP64 (the
-//      paper's absolute eps = 1e-8 lies below FP32 resolution of r).
+//      is the fallback); (A^T y)_j in FP64 is formed when atom j first enters a support;
+//      when |c| > M the minimum-norm solution s = A_c^T (A_c A_c^T)^{-1} y is used,
+//   5. prunes to kappa atoms by rank counting on the refined coefficients (and, for
+//      gOMP, refits on them),
+//   6. recomputes the residual r = y - A x in FP32 and decides Delta = ||r - r_prev|| <
+//      eps with the FP32 error bound of r: an unchanged iterate gives Delta = 0 exactly,
+//      and a Delta too close to eps for the bound is recomputed in FP64 from the change
+//      of x (the paper's absolute eps = 1e-8 lies below FP32 resolution of r).
+// FP64 arithmetic is left to the least squares' residuals and right-hand sides (one
+// instruction per product on a pipe the FP32 work leaves free) and to the rare cases that
+// need it (a certification band, an ambiguous Delta, a failed FP32 factor): the
+// correlation and the residual, which once took most of the FP64 work, run in FP32.
 // Every step is deterministic and a support keeps its order, so an unchanged support
 // reproduces x bit for bit and Delta = 0 exactly, as in the paper's stopping rule; for the
 // same reason BIHT and CoSaMP may stop at a repeated iterate (the rest of the run is
@@ -44,11 +51,11 @@ constexpr int kNK = kMaxN / 32;  // atoms per lane
 // pixels [pix0, pix0 + P).
 struct GrCube {
   int M, N;
-  const double* A64;   // M x N
-  const float* A32;    // M x N
-  const double* At64;  // N x M
-  const double* G64;   // N x N
-  const float* G32;    // N x N FP32 rounding of G64, or nullptr (gathers then convert)
+  const float* A32;    // M x N, FP32 rounding of A
+  const float* At32;   // N x M, the same transposed (column j of A contiguous)
+  const double* At64;  // N x M, FP64
+  const float* G32;    // N x N, FP32 rounding of the Gram matrix A^T A
+  const double* G64;   // N x N, FP64 Gram matrix
   const float* Y;
   float* X;
   int64_t P, pix0;
@@ -83,8 +90,8 @@ struct GrParams {
 // sized for FP64 (the fallback factorisation then runs in place); otherwise they hold
 // the FP32 factors only and the fallback uses the warp's global slot.
 struct Layout {
-  int y, rf, r, xd, b, inc, c, q, sel, xq, L, invd, v, s, wv, Lq, invq, vq, sq,
-      svals, cx, cq, ring, total;
+  int y, rf, xd, b32, bx, bk, inc, c, q, qp, sel, xq, xqp, xqf, L, invd, v, s, wv, Lq, invq,
+      vq, sq, svals, cx, cq, ring, total;
   __host__ __device__ Layout(int M, int N, int cmax, int dmax, int kmax, int selmax,
                              bool fp64_smem, bool need_q, bool need_cyc, bool need_xd,
                              int d32) {
@@ -96,8 +103,9 @@ struct Layout {
       o += bytes;
       return at;
     };
-    b = take(8 * N, 8);
+    bx = take(8 * N, 8);  // A^T y in FP64, filled in for support atoms
     xq = take(8 * kmax, 8);
+    xqp = take(8 * kmax, 8);  // the previous iterate's kept coefficients (Delta)
     const int df = fp64_smem ? dmax : d32;  // factor rows held here
     L = take(fw * (df * (df + 1) / 2), 8);
     invd = take(fw * df, 8);
@@ -113,15 +121,18 @@ struct Layout {
     const int kc = need_cyc ? kmax : 0;  // saved iterate of the cycle search
     cx = take(8 * kc, 8);
     ring = take(need_cyc ? 8 * 32 : 0, 8);  // hashes of the last 32 iterates
-    r = take(8 * M, 8);
-    y = take(8 * M, 8);
-    rf = take(4 * M, 4);
+    y = take(4 * M, 4);
+    rf = take(4 * M, 4);   // FP32 residual of the current iterate
+    b32 = take(4 * N, 4);  // A^T y in FP32 (the correlation)
+    xqf = take(4 * kmax, 4);  // FP32 copies of xq (the correlation and the residual)
     xd = take(need_xd ? 4 * N : 0, 4);  // FP32 x row (BIHT's u = x + mu A^T r)
     c = take(2 * cmax, 2);
     q = take(2 * kmax, 2);
+    qp = take(2 * kmax, 2);
     cq = take(2 * kc, 2);
     sel = take(2 * selmax, 2);  // a selection: G, 2 kappa or kappa atoms, or kappa positions
     inc = take(N, 1);
+    bk = take(N, 1);  // bx[j] holds A^T y for atom j
     total = (o + 15) / 16 * 16;
   }
 };
@@ -134,38 +145,58 @@ struct Warp {
   const GrParams& p;
   int lane;
   const GrCube* cb;  // the cube of the pixel in hand (device table entry)
-  float *rf, *xd;
-  double *y, *r, *b, *xq, *L, *invd, *v, *s, *wv, *Lq, *invq, *vq, *sq, *svals;
-  uint8_t* inc;
-  int16_t *c, *q, *sel;
+  float *y, *rf, *xd, *b32, *xqf;
+  double *bx, *xq, *xqp, *L, *invd, *v, *s, *wv, *Lq, *invq, *vq, *sq, *svals;
+  uint8_t *inc, *bk;
+  int16_t *c, *q, *qp, *sel;
   double* fb;  // this warp's global FP64 fallback slot, or nullptr
 };
 
-// (A^T y)_j in FP64, computed for every atom when the pixel starts (load_rhs).
-__device__ __forceinline__ double rhs(Warp& w, int j) { return w.b[j]; }
+// (A^T y)_j in FP64 (computed by ensure_rhs before any use).
+__device__ __forceinline__ double rhs(Warp& w, int j) { return w.bx[j]; }
 
-// b = A^T y in FP64 for every atom: lanes own atoms, rows of A are read coalesced, and
-// each b_j sums its M products in the order m = 0, 1, ...
-__device__ void load_rhs(Warp& w) {
+// b32 = A^T y in FP32 for every atom (the correlation's first term): lanes own atoms,
+// rows of A are read coalesced, each sum in the order m = 0, 1, ...
+__device__ void load_rhs32(Warp& w) {
   const int N = w.cb->N, M = w.cb->M;
-  double acc[kNK];
+  float acc[kNK];
 #pragma unroll
-  for (int kk = 0; kk < kNK; ++kk) acc[kk] = 0.0;
+  for (int kk = 0; kk < kNK; ++kk) acc[kk] = 0.f;
   for (int m = 0; m < M; ++m) {
-    const double ym = w.y[m];
-    const double* arow = w.cb->A64 + (size_t)m * N;
+    const float ym = w.y[m];
+    const float* arow = w.cb->A32 + (size_t)m * N;
 #pragma unroll
     for (int kk = 0; kk < kNK; ++kk) {
       const int n = w.lane + 32 * kk;
-      if (n < N) acc[kk] = fma(__ldg(arow + n), ym, acc[kk]);
+      if (n < N) acc[kk] = fmaf(__ldg(arow + n), ym, acc[kk]);
     }
   }
 #pragma unroll
   for (int kk = 0; kk < kNK; ++kk) {
     const int n = w.lane + 32 * kk;
-    if (n < N) w.b[n] = acc[kk];
+    if (n < N) w.b32[n] = acc[kk];
   }
   __syncwarp();
+}
+
+// (A^T y)_j in FP64 for every atom of atoms[0..n) not yet known: the M products of
+// column j of A with y, lanes over the rows (contiguous in A^T), summed across the warp.
+__device__ void ensure_rhs(Warp& w, const int16_t* atoms, int n) {
+  const int M = w.cb->M;
+  for (int t = 0; t < n; ++t) {
+    const int j = atoms[t];
+    if (w.bk[j]) continue;  // warp-uniform (shared-memory broadcast)
+    const double* a = w.cb->At64 + (size_t)j * M;
+    double acc = 0.0;
+    for (int m = w.lane; m < M; m += 32) acc = fma(__ldg(a + m), (double)w.y[m], acc);
+    acc = warp_sum(acc);
+    __syncwarp();
+    if (w.lane == 0) {
+      w.bx[j] = acc;
+      w.bk[j] = 1;
+    }
+    __syncwarp();
+  }
 }
 
 // Appends row n to the factor L of a growing normal-equation system.  g(t) gives the
@@ -228,7 +259,7 @@ __device__ void back_solve(Warp& w, const double* L, const double* invd, const d
 // Mixed-precision support least squares: FP32 Cholesky of G_c, FP32 triangular solves
 // on vectors held in registers (lane l owns entries l, l+32, ...), and FP64 iterative
 // refinement s <- s + G_c^{-1}(b - G_c s) whose residual uses the FP64 Gram matrix.
-// FP64 work per solve is one or two n^2 residuals instead of an n^3/3 factorisation,
+// FP64 work per solve is one n^2 residual (rarely two) instead of an n^3/3 factorisation,
 // which matters on GB300, whose FP64 rate is 1/64 of its FP32 rate.
 // ---------------------------------------------------------------------------------
 template <int VR, typename T>
@@ -244,17 +275,6 @@ __device__ __forceinline__ float warp_max(float v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
   return v;
-}
-__device__ __forceinline__ double warp_max(double v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
-  return v;
-}
-
-// (A^T y)_j for every atom of atoms[0..n) into out[0..n).
-__device__ void fill_rhs(Warp& w, const int16_t* atoms, int n, double* out) {
-  for (int t = w.lane; t < n; t += 32) out[t] = w.b[atoms[t]];
-  __syncwarp();
 }
 
 // FP32 factors are packed row-major lower triangles: entry (i, k), k <= i, at
@@ -279,7 +299,6 @@ __device__ bool chol32(Warp& w, float* L, float* invd, int n, const int16_t* ato
   // several columns of loads are in flight before their stores
   constexpr int kB = 4;
   const float* G32 = w.cb->G32;
-  const double* G64 = w.cb->G64;
   for (int k0 = 0; k0 < n; k0 += kB) {
     float g[kB][VR];
 #pragma unroll
@@ -291,7 +310,7 @@ __device__ bool chol32(Warp& w, float* L, float* invd, int n, const int16_t* ato
         const int i = k + lane + 32 * r;
         const int col = atoms[min(i, n - 1)];  // clamped lanes are not stored
         g[kk][r] = 0.f;
-        if (k + 32 * r < n) g[kk][r] = G32 ? __ldg(G32 + row + col) : (float)__ldg(G64 + row + col);
+        if (k + 32 * r < n) g[kk][r] = __ldg(G32 + row + col);
       }
     }
 #pragma unroll
@@ -419,19 +438,25 @@ __device__ void bwd32(const float* L, const float* invd, int n, float (&v)[VR], 
 }
 
 // Iterative refinement on the FP32 factor: returns true once a correction falls below
-// 1e-9 of the solution (the solution then carries FP64-level accuracy), false if the
+// 1e-9 of the solution (the solution then carries FP64 accuracy: the next correction,
+// about cond(G_c) 2^-24 times this one, is below FP64 resolution), false if the
 // corrections stop contracting (the system is too ill-conditioned for an FP32 factor).
+// A solution only FP32-corrected once (about 1e-14 relative) would be cheaper, but it
+// can turn an exact tie of the FP64 iterate, as in small integer examples, the other
+// way.  The right-hand side is (A^T y)_c from w.bx.
 template <int VR>
 __device__ bool refine32(Warp& w, const float* L, const float* invd, int n,
-                         const int16_t* atoms, const double* b, double* s) {
+                         const int16_t* atoms, double* s) {
   const int lane = w.lane, N = w.cb->N;
   const double* G = w.cb->G64;
   double sr[VR], rr[VR];
+  int col[VR];
 #pragma unroll
   for (int k = 0; k < VR; ++k) {
-    int t = lane + 32 * k;
+    const int t = lane + 32 * k;
+    col[k] = atoms[min(t, n - 1)];
     sr[k] = 0.0;
-    rr[k] = t < n ? b[t] : 0.0;
+    rr[k] = t < n ? w.bx[col[k]] : 0.0;
   }
   float prev = 3.0e38f, smax = 0.f;  // smax: max |s| of the first solve, the test's scale
   for (int step = 0; step < 5; ++step) {
@@ -459,13 +484,11 @@ __device__ bool refine32(Warp& w, const float* L, const float* invd, int n,
     // r = b - G_c s in FP64; by symmetry lane t reads G(c_j, c_t) from row c_j, so a
     // warp's loads fall in one row at the sorted atoms; eight rows of loads in flight
     {
-      int col[VR];
       double acc[VR][2];
 #pragma unroll
       for (int k = 0; k < VR; ++k) {
         const int t = lane + 32 * k;
-        col[k] = atoms[min(t, n - 1)];
-        acc[k][0] = t < n ? b[t] : 0.0;
+        acc[k][0] = t < n ? w.bx[col[k]] : 0.0;
         acc[k][1] = 0.0;
       }
       constexpr int kB = VR <= 2 ? 8 : 4;
@@ -500,7 +523,6 @@ __device__ bool chol32_append(Warp& w, float* L, float* invd, int nf, int n,
                               const int16_t* atoms) {
   const int lane = w.lane, N = w.cb->N;
   const float* G32 = w.cb->G32;
-  const double* G64 = w.cb->G64;
   for (int i = nf; i < n; ++i) {
     const size_t row = (size_t)atoms[i] * N;
     float g[VR];
@@ -508,10 +530,10 @@ __device__ bool chol32_append(Warp& w, float* L, float* invd, int nf, int n,
     for (int k = 0; k < VR; ++k) {
       const int t = lane + 32 * k;
       const int col = atoms[min(t, i)];
-      const float v = G32 ? __ldg(G32 + row + col) : (float)__ldg(G64 + row + col);
+      const float v = __ldg(G32 + row + col);
       g[k] = t < i ? v : 0.f;
     }
-    const float gii = G32 ? __ldg(G32 + row + atoms[i]) : (float)__ldg(G64 + row + atoms[i]);
+    const float gii = __ldg(G32 + row + atoms[i]);
     fwd32<VR>(L, invd, i, g, lane);  // g := L_{0:i}^{-1} g
     float ss = 0.f;
 #pragma unroll
@@ -742,10 +764,9 @@ __device__ bool ls_fresh(Warp& w, const int16_t* atoms, int n, double* L, double
 template <int VR>
 __device__ bool ls_solve(Warp& w, const int16_t* atoms, int n, double* Lbuf, double* invdbuf,
                          double* vbuf, double* s, int cap) {
-  fill_rhs(w, atoms, n, vbuf);
   float* L32 = reinterpret_cast<float*>(Lbuf);
   float* inv32 = reinterpret_cast<float*>(invdbuf);
-  if (chol32<VR>(w, L32, inv32, n, atoms) && refine32<VR>(w, L32, inv32, n, atoms, vbuf, s))
+  if (chol32<VR>(w, L32, inv32, n, atoms) && refine32<VR>(w, L32, inv32, n, atoms, s))
     return true;
   // FP64 fallback: in place when the shared regions are FP64-sized, else in the warp's
   // global slot (capacity dmax >= n)
@@ -763,7 +784,6 @@ __device__ bool ls_solve(Warp& w, const int16_t* atoms, int n, double* Lbuf, dou
 template <int VR>
 __device__ bool ls_solve_grow(Warp& w, const int16_t* atoms, int& nf, int n, double* Lbuf,
                               double* invdbuf, double* vbuf, double* s, int cap) {
-  fill_rhs(w, atoms, n, vbuf);
   if (n > w.p.d32 && w.fb) {
     // the support outgrew the shared-memory factor: FP64 in the warp's global slot
     nf = 0;
@@ -775,7 +795,7 @@ __device__ bool ls_solve_grow(Warp& w, const int16_t* atoms, int& nf, int n, dou
   float* inv32 = reinterpret_cast<float*>(invdbuf);
   const bool factored = chol32_append<VR>(w, L32, inv32, nf, n, atoms);
   nf = factored ? n : 0;
-  if (factored && refine32<VR>(w, L32, inv32, n, atoms, vbuf, s)) return true;
+  if (factored && refine32<VR>(w, L32, inv32, n, atoms, s)) return true;
   if (w.fb) {
     const int D = w.p.dmax;
     double* Lg = w.fb;
@@ -807,25 +827,19 @@ __device__ bool ls_min_norm(Warp& w, const int16_t* atoms, int n, double* s) {
           }
           return h;
         },
-        w.y[k]);
+        (double)w.y[k]);
     if (!ok) return false;
   }
   double* zv = w.svals;  // z = H^{-1} y
   back_solve(w, L, invd, v, zv, cap, M);
   for (int j = w.lane; j < n; j += 32) {
-    const double* a = At + (size_t)atoms[j] * M;
     double acc = 0.0;
+    const double* a = At + (size_t)atoms[j] * M;
     for (int m = 0; m < M; ++m) acc += a[m] * zv[m];
     s[j] = acc;
   }
   __syncwarp();
   return true;
-}
-
-// sqrt(ss) in FP32, rounded up with a margin for the conversion of ss: an upper bound of
-// the FP64 norm, which is all the FP32 error bound of the correlation needs.
-__device__ __forceinline__ float norm_up(double ss) {
-  return __fsqrt_ru(__double2float_ru(ss)) * 1.000001f;
 }
 
 // SplitMix64's output mixing function (Steele, Lea and Flood, OOPSLA 2014).
@@ -856,12 +870,14 @@ __global__ void __launch_bounds__(256, 2) k_greedy(GrParams p) {
              ALGO == kGomp, ALGO != kGomp, ALGO == kBiht, p.d32);
   unsigned char* base = gsm + (size_t)wid * p.warp_bytes;
   Warp w{p, lane, p.cubes};
-  w.y = (double*)(base + lay.y);
+  w.y = (float*)(base + lay.y);
   w.rf = (float*)(base + lay.rf);
-  w.r = (double*)(base + lay.r);
   w.xd = (float*)(base + lay.xd);
-  w.b = (double*)(base + lay.b);
+  w.b32 = (float*)(base + lay.b32);
+  w.xqf = (float*)(base + lay.xqf);
+  w.bx = (double*)(base + lay.bx);
   w.xq = (double*)(base + lay.xq);
+  w.xqp = (double*)(base + lay.xqp);
   w.L = (double*)(base + lay.L);
   w.invd = (double*)(base + lay.invd);
   w.v = (double*)(base + lay.v);
@@ -876,18 +892,22 @@ __global__ void __launch_bounds__(256, 2) k_greedy(GrParams p) {
   int16_t* const cyc_q = (int16_t*)(base + lay.cq);
   unsigned long long* const ring = (unsigned long long*)(base + lay.ring);
   w.inc = base + lay.inc;
+  w.bk = base + lay.bk;
   w.c = (int16_t*)(base + lay.c);
   w.q = (int16_t*)(base + lay.q);
+  w.qp = (int16_t*)(base + lay.qp);
   w.sel = (int16_t*)(base + lay.sel);
   w.fb = p.fb64 ? p.fb64 + (size_t)(blockIdx.x * (blockDim.x >> 5) + wid) * p.fb_slot : nullptr;
 
   for (int n = lane; n < p.Nmax; n += 32) {
     if (ALGO == kBiht) w.xd[n] = 0.f;
     w.inc[n] = 0;
+    w.bk[n] = 0;
   }
   __syncwarp();
   int cur = -1;        // cube whose data w.cb holds
-  float cnorm = 0.f;  // its largest column norm, rounded up
+  float cnorm = 0.f;   // its largest column norm, rounded up
+  constexpr float u32 = 0x1p-24f;
 
   for (;;) {
     unsigned long long pix_u = 0;
@@ -908,15 +928,16 @@ __global__ void __launch_bounds__(256, 2) k_greedy(GrParams p) {
     if (ci != cur) {
       w.cb = p.cubes + ci;
       cur = ci;
-      // largest column norm of A (diagonal of the Gram matrix), for the FP32 error bound
-      // of the correlation
-      double cn2 = 0.0;
-      for (int n = lane; n < w.cb->N; n += 32) cn2 = fmax(cn2, w.cb->G64[(size_t)n * w.cb->N + n]);
-      cnorm = norm_up(warp_max(cn2));
+      // largest column norm of A (square root of the Gram matrix's largest diagonal
+      // entry), rounded up: the FP32 error bounds of the correlation and the residual
+      float cn2 = 0.f;
+      for (int n = lane; n < w.cb->N; n += 32) cn2 = fmaxf(cn2, w.cb->G32[(size_t)n * w.cb->N + n]);
+      cnorm = __fsqrt_ru(warp_max(cn2) * 1.0000005f) * 1.000001f;
     }
     const GrCube& cb = *w.cb;
     const int M = cb.M, N = cb.N;
     const int64_t pix = (int64_t)pix_u - cb.pix0;
+    const float gmax = cnorm * cnorm * 1.000001f;  // bounds every |(A^T A)_jk|
 
     // a per-pixel level outside 0..kappa bound is clamped: the workspace holds kmax atoms
     const int kappa = cb.kappa_pp ? min(max((int)cb.kappa_pp[pix], 0), p.kmax) : p.kappa;
@@ -927,22 +948,25 @@ __global__ void __launch_bounds__(256, 2) k_greedy(GrParams p) {
       if (M / G < cap) cap = M / G;
     }
     bool bad = false;
-    double r2 = 0.0;
+    float y2 = 0.f;
     for (int m = lane; m < M; m += 32) {
       float yv = cb.Y[pix * M + m];
       bad |= !isfinite(yv);
       w.y[m] = yv;
-      w.r[m] = (double)yv;  // r^0 = y
-      w.rf[m] = yv;
-      r2 += (double)yv * yv;
+      w.rf[m] = yv;  // r^0 = y
+      y2 = fmaf(yv, yv, y2);
     }
-    if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(p.status, kStNonFinite);
-    float rnorm = norm_up(warp_sum(r2));  // ||r||_2, rounded up (the certification bound)
+    const bool bad_pixel = __any_sync(0xffffffffu, bad);
+    if (bad_pixel && lane == 0) atomicOr(p.status, kStNonFinite);
+    // ||y||_2 rounded up (with room for the M roundings of the sum of squares)
+    const float ynorm = __fsqrt_ru(warp_sum(y2) * (1.f + (M + 2) * u32)) * 1.000001f;
     __syncwarp();
-    if (!p.start_done && cap > 0) load_rhs(w);
+    if (!p.start_done && cap > 0) load_rhs32(w);
 
-    int nc = 0, nq = 0, it = 0;
+    int nc = 0, nq = 0, nqp = 0, it = 0;
     int nf = 0;  // gOMP: rows of the FP32 factor of G_c carried over between iterations
+    float x1 = 0.f;     // sum |x_q| of the current iterate, rounded up
+    float rerr = 0.f;   // error bound of the FP32 residual of the current iterate (r^0 = y)
     uint8_t conv = 0;
     // cycle search over the iterates x_it (BIHT, CoSaMP): ring[it % 32] holds a hash of
     // x_it; a hash seen `period` iterations ago nominates a cycle, which is confirmed by
@@ -959,20 +983,30 @@ __global__ void __launch_bounds__(256, 2) k_greedy(GrParams p) {
     double work = 0.0;
     bool fail = false;
     while (!p.start_done && it < cap) {
-      // ---- step 1: correlation (u = x + mu p for BIHT) ----
+      // ---- step 1: correlation p = A^T r = A^T y - (A^T A)_{:,q} x_q (u = x + mu p for
+      //      BIHT): lane l owns atoms l + 32 kk; row q_t of the Gram matrix is column q_t
       float val[kNK];
 #pragma unroll
-      for (int kk = 0; kk < kNK; ++kk) val[kk] = 0.f;
-#pragma unroll 4
-      for (int m = 0; m < M; ++m) {
-        float rm = w.rf[m];
-        const float* arow = cb.A32 + (size_t)m * N;
+      for (int kk = 0; kk < kNK; ++kk) {
+        const int n = lane + 32 * kk;
+        val[kk] = n < N ? w.b32[n] : 0.f;
+      }
+#pragma unroll 2
+      for (int t = 0; t < nq; ++t) {
+        const float xt = w.xqf[t];
+        const float* grow = cb.G32 + (size_t)w.q[t] * N;
 #pragma unroll
         for (int kk = 0; kk < kNK; ++kk) {
-          int n = lane + 32 * kk;
-          if (n < N) val[kk] += arow[n] * rm;
+          const int n = lane + 32 * kk;
+          if (n < N) val[kk] = fmaf(-__ldg(grow + n), xt, val[kk]);
         }
       }
+      // FP32 error bound of p_j: A^T y errs by at most (M + 2) u ||A_j|| ||y|| (rounded A,
+      // M rounded FMAs), the |q| FMAs of the Gram part by (|q| + 3) u sum_t |G_jt| |x_t|
+      // <= (|q| + 3) u gmax ||x||_1 (rounded G and x included) plus |q| u |A^T y|; the 1%
+      // margin covers the FP32 evaluation of the bound itself
+      const float pbound =
+          ((M + nq + 2) * cnorm * ynorm + (nq + 3) * gmax * x1) * u32 * 1.01f;
       if (ALGO == kBiht) {
 #pragma unroll
         for (int kk = 0; kk < kNK; ++kk) {
@@ -984,10 +1018,16 @@ __global__ void __launch_bounds__(256, 2) k_greedy(GrParams p) {
       const float tk = ksel > 8 ? topk_select_atoms(w, val, N, ksel, w.sel)
                                 : topk_atoms(w, val, N, ksel, w.sel);
       {
-        // FP32 error bound of the correlation: the sum of M products of rounded A and r
-        // errs by at most (M + 2) u sum |A_mj r_m| <= (M + 2) u ||A_j|| ||r||, u = 2^-24
-        // (FP32 arithmetic: the 1% margin covers its own roundings)
-        const float pbound = (M + 4) * 0x1p-24f * 1.01f * cnorm * rnorm;
+        // the exact value of an atom's selection key, in FP64: p_j = (A^T y)_j -
+        // sum_t G(j, q_t) x_t (the certification's recompute of the band)
+        auto exact_p = [&](int j) {
+          const double* a = cb.At64 + (size_t)j * M;
+          const double* grow = cb.G64 + (size_t)j * N;
+          double g = 0.0;
+          for (int m = 0; m < M; ++m) g += a[m] * (double)w.y[m];
+          for (int t = 0; t < nq; ++t) g -= grow[w.q[t]] * w.xq[t];
+          return g;
+        };
         if (ALGO == kBiht) {
           // u = x + mu p adds the roundings of x, mu and of the update itself
           float um = 0.f, xm = 0.f;
@@ -1002,27 +1042,19 @@ __global__ void __launch_bounds__(256, 2) k_greedy(GrParams p) {
           um = warp_max(um);
           xm = warp_max(xm);
           const float mu_up = fabsf(p.mu) * 1.000001f;  // |mu| rounded to FP32, and up
-          const float E = mu_up * pbound + 0x1p-24f * 1.01f * (um + xm + mu_up * cnorm * rnorm);
+          // |p_j| <= ||A_j|| ||y|| + gmax ||x||_1 bounds the FP32 product's magnitude
+          const float pm = cnorm * ynorm + gmax * x1;
+          const float E = mu_up * pbound + u32 * 1.01f * (um + xm + mu_up * pm);
           certify_topk(w, val, N, ksel, tk, E * 1.001f,
                        [&](int j) {
-                         const double* a = cb.At64 + (size_t)j * M;
-                         double g = 0.0;
-                         for (int m = 0; m < M; ++m) g += a[m] * w.r[m];
                          double xj = 0.0;
                          for (int t = 0; t < nq; ++t)
                            if (w.q[t] == j) xj = w.xq[t];
-                         return xj + p.mu64 * g;
+                         return xj + p.mu64 * exact_p(j);
                        },
                        w.sel);
         } else {
-          certify_topk(w, val, N, ksel, tk, pbound * 1.001f,
-                       [&](int j) {
-                         const double* a = cb.At64 + (size_t)j * M;
-                         double g = 0.0;
-                         for (int m = 0; m < M; ++m) g += a[m] * w.r[m];
-                         return g;
-                       },
-                       w.sel);
+          certify_topk(w, val, N, ksel, tk, pbound * 1.001f, exact_p, w.sel);
         }
       }
 
@@ -1065,6 +1097,8 @@ __global__ void __launch_bounds__(256, 2) k_greedy(GrParams p) {
         nc = cnt;
         __syncwarp();
       }
+      // (A^T y)_c as FP32 pairs for the least squares (new atoms only)
+      ensure_rhs(w, w.c, nc);
 
       // ---- step 2: least squares on c ----
       const int nf0 = nf;
@@ -1092,9 +1126,13 @@ __global__ void __launch_bounds__(256, 2) k_greedy(GrParams p) {
       }
 
       // ---- step 3: prune to kappa (and refit for gOMP) ----
-      // previous support leaves xd
-      if (ALGO == kBiht)
-        for (int j = lane; j < nq; j += 32) w.xd[w.q[j]] = 0.f;
+      // the previous iterate, for Delta; BIHT's leaves xd
+      for (int j = lane; j < nq; j += 32) {
+        w.qp[j] = w.q[j];
+        w.xqp[j] = w.xq[j];
+        if (ALGO == kBiht) w.xd[w.q[j]] = 0.f;
+      }
+      nqp = nq;
       __syncwarp();
       int keep = nc < kappa ? nc : kappa;
       if (nc > kappa) {
@@ -1130,43 +1168,85 @@ __global__ void __launch_bounds__(256, 2) k_greedy(GrParams p) {
         __syncwarp();
         nc = nq;
       }
-      if (ALGO == kBiht)
-        for (int j = lane; j < nq; j += 32) w.xd[w.q[j]] = (float)w.xq[j];
+      // FP32 copies of x_q (the next correlation and the residual) and ||x||_1
+      float xs = 0.f;
+      for (int j = lane; j < nq; j += 32) {
+        const float xf = (float)w.xq[j];
+        w.xqf[j] = xf;
+        xs += fabsf(xf);
+        if (ALGO == kBiht) w.xd[w.q[j]] = xf;
+      }
+      x1 = warp_sum(xs) * (1.f + (nq + 2) * u32) * 1.000001f;
       __syncwarp();
 
-      // ---- step 4: r = y - A x, Delta (FP64) ----
-      double d2 = 0.0, rr = 0.0;
+      // ---- step 4: r = y - A x (FP32, lanes own rows m = lane + 32 kk; columns of A^T are
+      //      contiguous) and the stopping test Delta = ||r - r_prev|| < eps ----
+      float d2 = 0.f;
       {
-        // lanes own rows m = lane + 32 kk (M <= 128); atom columns of A^T are contiguous
-        double acc[4] = {0.0, 0.0, 0.0, 0.0};
+        float acc[4];
         const int mc = M - 1;
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk) acc[kk] = w.y[min(lane + 32 * kk, mc)];
 #pragma unroll 4
-        for (int j = 0; j < nq; ++j) {
-          const double* col = cb.At64 + (size_t)w.q[j] * M;
-          const double xj = w.xq[j];
+        for (int t = 0; t < nq; ++t) {
+          const float* col = cb.At32 + (size_t)w.q[t] * M;
+          const float xt = w.xqf[t];
 #pragma unroll
           for (int kk = 0; kk < 4; ++kk)
-            if (32 * kk < M) acc[kk] = fma(__ldg(col + min(lane + 32 * kk, mc)), xj, acc[kk]);
+            if (32 * kk < M) acc[kk] = fmaf(-__ldg(col + min(lane + 32 * kk, mc)), xt, acc[kk]);
         }
+        __syncwarp();
 #pragma unroll
         for (int kk = 0; kk < 4; ++kk) {
           const int m = lane + 32 * kk;
           if (m < M) {
-            double rn = w.y[m] - acc[kk];
-            double df = rn - w.r[m];
-            d2 += df * df;
-            rr += rn * rn;
-            w.r[m] = rn;
-            w.rf[m] = (float)rn;
+            const float df = acc[kk] - w.rf[m];
+            d2 = fmaf(df, df, d2);
+            w.rf[m] = acc[kk];
           }
         }
       }
       d2 = warp_sum(d2);
-      rnorm = norm_up(warp_sum(rr));
-      __syncwarp();
       work += 2.0 * M * nq;
       ++it;
-      if (d2 < p.eps2) {
+      // each FP32 residual errs from r = y - A x by at most (|q| + 3) u (||y|| + ||A_j||max
+      // ||x||_1) in norm (rounded A and x, |q| rounded FMAs)
+      const float rerr_now = (nq + 3) * u32 * (ynorm + cnorm * x1) * 1.01f;
+      bool done_now = false;
+      if (p.eps2 > 0.0) {
+        // an unchanged iterate reproduces r bit for bit: Delta = 0 exactly
+        bool same = nq == nqp;
+        if (same) {
+          bool eq = true;
+          for (int j = lane; j < nq; j += 32)
+            eq &= w.q[j] == w.qp[j] &&
+                  __double_as_longlong(w.xq[j]) == __double_as_longlong(w.xqp[j]);
+          same = __all_sync(0xffffffffu, eq);
+        }
+        if (same) {
+          done_now = true;
+        } else {
+          const float dl = sqrtf(d2);
+          const float E = (rerr_now + rerr) * 1.001f + dl * (M + 4) * u32;
+          const double hi = (double)dl + (double)E, lo = (double)dl - (double)E;
+          if (hi * hi < p.eps2) {
+            done_now = true;
+          } else if (!(lo > 0.0 && lo * lo >= p.eps2)) {
+            // too close to eps for the FP32 bound: Delta = ||A (x_it - x_it-1)|| in FP64
+            double dd = 0.0;
+            for (int m = lane; m < M; m += 32) {
+              double v = 0.0;
+              for (int t = 0; t < nq; ++t) v += cb.At64[(size_t)w.q[t] * M + m] * w.xq[t];
+              for (int t = 0; t < nqp; ++t) v -= cb.At64[(size_t)w.qp[t] * M + m] * w.xqp[t];
+              dd += v * v;
+            }
+            done_now = warp_sum(dd) < p.eps2;
+          }
+        }
+      }
+      rerr = rerr_now;
+      __syncwarp();
+      if (done_now) {
         conv = 1;
         break;
       }
@@ -1217,18 +1297,21 @@ __global__ void __launch_bounds__(256, 2) k_greedy(GrParams p) {
       conv = 2;
       if (lane == 0) atomicOr(p.status, kStNotSpd);
     }
+    if (bad_pixel) conv = 3;  // measurements not finite (also latched in the status word)
     // output and reset
     if (ALGO == kBiht) {
       for (int n = lane; n < N; n += 32) {
         cb.X[pix * N + n] = w.xd[n];
         w.xd[n] = 0.f;
         w.inc[n] = 0;
+        w.bk[n] = 0;
       }
     } else {
       // x = xq on the atoms q, zero elsewhere
       for (int n = lane; n < N; n += 32) {
         cb.X[pix * N + n] = 0.f;
         w.inc[n] = 0;
+        w.bk[n] = 0;
       }
       __syncwarp();
       for (int j = lane; j < nq; j += 32) cb.X[pix * N + w.q[j]] = (float)w.xq[j];
@@ -1275,16 +1358,36 @@ cudaError_t put_cubes(const GrCube* host, int n, GrCube* dst, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+// Every launch of a greedy kernel instance may use up to the device's opt-in maximum of
+// dynamic shared memory: the attribute is set once per (device, instance), under a
+// lock, so launches from several host threads (context calls and the allocation-free
+// call) never change it under one another.
+std::mutex g_attr_mu;
+std::vector<std::pair<int, const void*>> g_attr_done;
+cudaError_t allow_full_smem(const void* kern) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lk(g_attr_mu);
+  for (const auto& d : g_attr_done)
+    if (d.first == dev && d.second == kern) return cudaSuccess;
+  int mx = 0;
+  e = cudaDeviceGetAttribute(&mx, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  if (e == cudaSuccess) g_attr_done.emplace_back(dev, kern);
+  return e;
+}
+
 GrCube cube_of(const Ctx& c, const float* Y, float* X, int64_t P, const int16_t* kappa_pp,
                int32_t* iters_out, uint8_t* conv_out, int64_t pix0) {
   GrCube g{};
   g.M = c.M;
   g.N = c.N;
-  g.A64 = c.A64;
   g.A32 = c.A32;
+  g.At32 = c.At32;
   g.At64 = c.At64;
-  g.G64 = c.G64;
   g.G32 = c.G32;
+  g.G64 = c.G64;
   g.Y = Y;
   g.X = X;
   g.P = P;
@@ -1393,7 +1496,8 @@ cudaError_t run_greedy(Ctx& c, GreedyAlgo algo, const GreedyArgs& a, const GrCub
   if (e == cudaSuccess && c.work) e = cudaMemsetAsync(c.work, 0, sizeof(double), c.stream);
   if (e != cudaSuccess) return e;
   auto launch = [&](auto kern) {
-    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t ea = allow_full_smem(reinterpret_cast<const void*>(kern));
+    if (ea != cudaSuccess) return ea;
     int per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, warps * 32, smem);
     if (per_sm < 1) per_sm = 1;
@@ -1458,21 +1562,22 @@ cudaError_t launch_greedy_batch(Ctx& c0, GreedyAlgo algo, const GreedyCube* cube
 // all device memory already handed to its own pool, or in a phase where the
 // device-wide synchronisation of cudaMalloc/cudaFree is not acceptable.  They pass
 // the FP64 dictionary, the measurements and the output (their own device memory);
-// everything else the gOMP kernel reads -- the FP32 and transposed copies of A, the
-// FP64 Gram matrix A^T A, the work counter and a status word -- lives in the
-// file-scope array below, which every GPU that loads this library holds until exit.
+// everything else the gOMP kernel reads -- the FP32 copy of A, its transpose in FP32 and
+// FP64, the Gram matrix A^T A in FP32 and FP64, the work counter and a status word --
+// lives in the file-scope array below, which every GPU that loads this library holds
+// until exit (2 MiB; every shape the library accepts, M <= 128 and N <= 256, fits).
 // Each call re-derives that data, so all calls share one scratch: calls that overlap
 // on the GPU (different streams, different host threads) race and must be ordered by
 // the caller.
 // ---------------------------------------------------------------------------------
-constexpr size_t kNoAllocScratchBytes = (size_t)1 << 20;  // 1 MiB
+constexpr size_t kNoAllocScratchBytes = (size_t)2 << 20;  // 2 MiB
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
 namespace cs {
 namespace {
 
 struct NoAllocLayout {
-  size_t counter, status, A32, At32, At64, G64, cube, total;
+  size_t counter, status, A32, At32, At64, G32, G64, cube, total;
   NoAllocLayout(int M, int N) {
     size_t o = 0;
     auto take = [&](size_t bytes) {
@@ -1485,32 +1590,35 @@ struct NoAllocLayout {
     A32 = take(sizeof(float) * (size_t)M * N);
     At32 = take(sizeof(float) * (size_t)M * N);
     At64 = take(sizeof(double) * (size_t)M * N);
+    G32 = take(sizeof(float) * (size_t)N * N);
     G64 = take(sizeof(double) * (size_t)N * N);
     cube = take(sizeof(GrCube));
     total = o;
   }
 };
 
-// FP32 copy of A, its transposes in FP32 and FP64 (same values as the context setup).
+// FP32 copy of A and its transposes in FP32 and FP64 (same values as the context setup).
 __global__ void k_noalloc_casts(int M, int N, const double* A, float* A32, float* At32,
                                 double* At64) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= M * N) return;
   int m = i / N, n = i % N;
-  double a = A[i];
+  const double a = A[i];
   A32[i] = (float)a;
-  At64[n * M + m] = a;
   At32[n * M + m] = (float)a;
+  At64[n * M + m] = a;
 }
 
-// G[r][c] = sum_k A[k][r] A[k][c], summed in the same order as the context setup.
-__global__ void k_noalloc_gram(int M, int N, const double* A, double* G) {
+// G[r][c] = sum_k A[k][r] A[k][c] in FP64, summed in the same order as the context
+// setup, and its FP32 rounding.
+__global__ void k_noalloc_gram(int M, int N, const double* A, float* G32, double* G64) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N * N) return;
   int r = i / N, col = i % N;
   double s = 0.0;
   for (int k = 0; k < M; ++k) s += A[r + k * N] * A[k * N + col];
-  G[i] = s;
+  G64[i] = s;
+  G32[i] = (float)s;
 }
 
 // Device address of g_noalloc_scratch on the current device, looked up once per device.
@@ -1546,13 +1654,14 @@ cudaError_t launch_gomp_noalloc(const double* A64, int M, int N, const GreedyArg
   float* A32 = reinterpret_cast<float*>(s + lay.A32);
   float* At32 = reinterpret_cast<float*>(s + lay.At32);
   double* At64 = reinterpret_cast<double*>(s + lay.At64);
+  float* G32 = reinterpret_cast<float*>(s + lay.G32);
   double* G64 = reinterpret_cast<double*>(s + lay.G64);
   // the counter and the status word must start at zero on every call
   e = cudaMemsetAsync(s + lay.counter, 0, 16, stream);
   if (e != cudaSuccess) return e;
   if (a.P == 0) return cudaSuccess;
   k_noalloc_casts<<<(M * N + 255) / 256, 256, 0, stream>>>(M, N, A64, A32, At32, At64);
-  k_noalloc_gram<<<(N * N + 255) / 256, 256, 0, stream>>>(M, N, A64, G64);
+  k_noalloc_gram<<<(N * N + 255) / 256, 256, 0, stream>>>(M, N, A64, G32, G64);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
 
@@ -1562,11 +1671,11 @@ cudaError_t launch_gomp_noalloc(const double* A64, int M, int N, const GreedyArg
   GrCube cube{};
   cube.M = M;
   cube.N = N;
-  cube.A64 = A64;
   cube.A32 = A32;
+  cube.At32 = At32;
   cube.At64 = At64;
+  cube.G32 = G32;
   cube.G64 = G64;
-  cube.G32 = nullptr;  // the factor gathers convert from G64
   cube.Y = a.Y;
   cube.X = a.X;
   cube.P = a.P;
@@ -1594,7 +1703,7 @@ cudaError_t launch_gomp_noalloc(const double* A64, int M, int N, const GreedyArg
   if (warps < 1) return cudaErrorInvalidConfiguration;
   size_t smem = (size_t)warps * wl.total;
   auto kern = greedy_kernel<kGomp>((p.dmax + 31) / 32);
-  e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  e = allow_full_smem(reinterpret_cast<const void*>(kern));
   if (e != cudaSuccess) return e;
   int per_sm = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, warps * 32, smem);
