@@ -291,7 +291,8 @@ __device__ __forceinline__ int ridx(int i, int k) { return (i * (i + 1) >> 1) + 
 // are finished in order: t_i,c -= L(i, j+c') L(j+c, j+c') for the block's earlier
 // columns c' (shuffled from the owners of rows j+c), L(j+c, j+c) = sqrt(t_{j+c},c) and
 // L(i, j+c) = t_i,c / L(j+c, j+c).  Returns false when a pivot drops below 1e-4 of its
-// original diagonal (FP32 would lose the factor).  invd ends up holding 1 / L(j, j).
+// original diagonal (FP32 would lose the factor).  The factor is left in the unit form
+// the solves use: U (unit lower triangle, packed as L) and invd(j) = 1 / L(j, j)^2.
 template <int VR>
 __device__ bool chol32(Warp& w, float* L, float* invd, int n, const int16_t* atoms) {
   const int lane = w.lane, N = w.cb->N;
@@ -393,48 +394,74 @@ __device__ bool chol32(Warp& w, float* L, float* invd, int n, const int16_t* ato
     }
     __syncwarp();
   }
+  // unit form for the solves: U(i, k) = L(i, k) / L(k, k) below the diagonal and
+  // invd(k) = 1 / L(k, k)^2 (G_c = U D U^T with D = diag(L(k, k)^2))
+#pragma unroll
+  for (int r = 0; r < VR; ++r) {
+    const int i = lane + 32 * r;
+    if (32 * r < n) {
+      for (int k = 0; k < n - 1; ++k)
+        if (k < i && i < n) L[base[r] + k] *= invd[k];
+    }
+  }
+  __syncwarp();
+  for (int k = lane; k < n; k += 32) invd[k] = invd[k] * invd[k];
+  __syncwarp();
   return true;
 }
 
-// v := L^{-1} v (column sweeps: lanes t > i read L(t, i)) and v := L^{-T} v (row sweeps:
-// lanes t < i read L(i, t)) on register-distributed vectors.
+// Solves with G_c = U D U^T, U unit lower triangular (packed rows, the diagonal slot
+// unused) and d2 = diag(D)^-1, on register-distributed vectors (lane l owns rows l,
+// l+32, ...).  v := U^{-1} v by column sweeps (lanes t > i read U(t, i)); v := U^{-T} v
+// by row sweeps (lanes t < i read U(i, t)).  With a unit diagonal, each step of a sweep
+// is a shuffle and one FMA per owned row: the row's value needs no division, and rows
+// that must not change multiply a zero.  Reads past the stored rows (lanes of rows >= n,
+// or past row i's last entry) stay inside the triangle region and are multiplied by
+// zero or land in rows >= n, which no one reads.
 template <int VR>
-__device__ void fwd32(const float* L, const float* invd, int n, float (&v)[VR], int lane) {
-  // rows of slot S (i in [32S, 32S + 32)) come from lane i - 32S's v[S]; slots below S
-  // hold rows < i and stay, slot S updates its rows past i, slots above S all their rows
+__device__ void fwd_unit(const float* U, int n, float (&v)[VR], int lane) {
+  int base[VR];
+#pragma unroll
+  for (int k = 0; k < VR; ++k) base[k] = ridx(min(lane + 32 * k, n > 0 ? n - 1 : 0), 0);
 #pragma unroll
   for (int S = 0; S < VR; ++S) {
+    if (32 * S >= n) break;  // warp-uniform
     const int iend = min(n, 32 * S + 32);
+    const int t = lane + 32 * S;
     for (int i = 32 * S; i < iend; ++i) {
-      const float vi = __shfl_sync(0xffffffffu, v[S], i - 32 * S) * invd[i];
-      const int t = lane + 32 * S;
-      if (t == i) v[S] = vi;
-      else if (t > i && t < n) v[S] = fmaf(-L[ridx(t, i)], vi, v[S]);
+      const float zi = __shfl_sync(0xffffffffu, v[S], i - 32 * S);
+      const float l = t > i ? U[base[S] + i] : 0.f;
+      v[S] = fmaf(-l, zi, v[S]);
 #pragma unroll
-      for (int k = S + 1; k < VR; ++k) {
-        const int tk = lane + 32 * k;
-        if (tk < n) v[k] = fmaf(-L[ridx(tk, i)], vi, v[k]);
-      }
+      for (int k = S + 1; k < VR; ++k) v[k] = fmaf(-U[base[k] + i], zi, v[k]);
     }
   }
 }
 template <int VR>
-__device__ void bwd32(const float* L, const float* invd, int n, float (&v)[VR], int lane) {
-  // rows from the last down: slot S's rows update the rows below them in slot S and all
-  // rows of the slots below S
+__device__ void bwd_unit(const float* U, int n, float (&v)[VR], int lane) {
 #pragma unroll
   for (int S = VR - 1; S >= 0; --S) {
+    if (32 * S >= n) continue;  // warp-uniform
     const int iend = min(n, 32 * S + 32);
+    const int t = lane + 32 * S;
     for (int i = iend - 1; i >= 32 * S; --i) {
-      const float si = __shfl_sync(0xffffffffu, v[S], i - 32 * S) * invd[i];
-      const float* row = L + ridx(i, 0);
-      const int t = lane + 32 * S;
-      if (t == i) v[S] = si;
-      else if (t < i) v[S] = fmaf(-row[t], si, v[S]);
+      const float si = __shfl_sync(0xffffffffu, v[S], i - 32 * S);
+      const float* row = U + ridx(i, 0);
+      const float l = t < i ? row[min(t, i)] : 0.f;
+      v[S] = fmaf(-l, si, v[S]);
 #pragma unroll
       for (int k = 0; k < S; ++k) v[k] = fmaf(-row[lane + 32 * k], si, v[k]);
     }
   }
+}
+// v := G_c^{-1} v
+template <int VR>
+__device__ __forceinline__ void solve_unit(const float* U, const float* d2, int n, float (&v)[VR],
+                                           int lane) {
+  fwd_unit<VR>(U, n, v, lane);
+#pragma unroll
+  for (int k = 0; k < VR; ++k) v[k] *= d2[min(lane + 32 * k, n - 1)];
+  bwd_unit<VR>(U, n, v, lane);
 }
 
 // Iterative refinement on the FP32 factor: returns true once a correction falls below
@@ -463,8 +490,7 @@ __device__ bool refine32(Warp& w, const float* L, const float* invd, int n,
     float f[VR];
 #pragma unroll
     for (int k = 0; k < VR; ++k) f[k] = (float)rr[k];
-    fwd32<VR>(L, invd, n, f, lane);
-    bwd32<VR>(L, invd, n, f, lane);
+    solve_unit<VR>(L, invd, n, f, lane);
     float dm = 0.f;
 #pragma unroll
     for (int k = 0; k < VR; ++k) {
@@ -514,9 +540,10 @@ __device__ bool refine32(Warp& w, const float* L, const float* invd, int n,
   return false;
 }
 
-// Extends the FP32 factor of G_c from its first nf rows to n rows, for atoms appended at
-// the end of c (gOMP's growing support): row i is w = L_{0:i}^{-1} G(c_{0:i}, c_i), one
-// forward sweep with the factor built so far, and L(i, i) = sqrt(G(c_i, c_i) - ||w||^2).
+// Extends the unit-form FP32 factor of G_c (U, d2 = invd) from its first nf rows to n
+// rows, for atoms appended at the end of c (gOMP's growing support): for row i,
+// z = U_{0:i}^{-1} G(c_{0:i}, c_i) by one forward sweep with the factor built so far,
+// U(i, k) = z_k d2_k, pivot D(i) = G(c_i, c_i) - sum_k z_k^2 d2_k and d2_i = 1 / D(i).
 // Returns false when a pivot drops below 1e-4 of its diagonal.
 template <int VR>
 __device__ bool chol32_append(Warp& w, float* L, float* invd, int nf, int n,
@@ -534,23 +561,20 @@ __device__ bool chol32_append(Warp& w, float* L, float* invd, int nf, int n,
       g[k] = t < i ? v : 0.f;
     }
     const float gii = __ldg(G32 + row + atoms[i]);
-    fwd32<VR>(L, invd, i, g, lane);  // g := L_{0:i}^{-1} g
+    fwd_unit<VR>(L, i, g, lane);  // g := U_{0:i}^{-1} g
     float ss = 0.f;
 #pragma unroll
     for (int k = 0; k < VR; ++k) {
       const int t = lane + 32 * k;
       if (t < i) {
-        ss = fmaf(g[k], g[k], ss);
-        L[ridx(i, t)] = g[k];
+        const float u = g[k] * invd[t];
+        ss = fmaf(g[k], u, ss);
+        L[ridx(i, t)] = u;
       }
     }
     const float d = gii - warp_sum(ss);
     if (!(d > 1e-4f * gii)) return false;  // warp-uniform
-    const float inv = rsqrtf(d);
-    if (lane == 0) {
-      L[ridx(i, i)] = d * inv;
-      invd[i] = inv;
-    }
+    if (lane == 0) invd[i] = 1.f / d;
     __syncwarp();
   }
   return true;
