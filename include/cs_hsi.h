@@ -48,9 +48,17 @@ typedef enum {
   CS_ERR_NO_DEVICE = 8   /* no CUDA device of compute capability 10.3 */
 } cs_status;
 
-/* Arithmetic of the correlation products A z and A^T r.  CS_FP32 is the plain FP32
- * path.  The others run the correlation on the tensor cores and win accuracy back
- * with an FP32 residual recompute and a refinement pass (see each call). */
+/* Arithmetic of FISTA's and ADMM's products with A.  CS_FP32 is the plain FP32 (SIMT)
+ * path.  CS_BF16 runs the products on the tcgen05 tensor cores with every operand split
+ * into BF16 hi + lo parts (hi*hi + lo*hi + hi*lo, FP32 accumulation: about 16 bits of
+ * each operand), where a kernel for the shape exists; cs_get_last_precision reports
+ * which arithmetic a call used.  CS_FP8_E4M3 is rejected (CS_ERR_ARG) by every call:
+ * per-tensor-scaled E4M3 products leave FISTA's 300-iteration iterate about 9e-2 from
+ * the FP64 result (3.5e-2 with the last 100 iterations on split BF16), far from the
+ * rel-L2 1e-3 bar, and the greedy calls' correlation, the only product FP8 could serve
+ * there, takes under 5% of their time.  The greedy calls compute one way whatever prec
+ * says: FP32 correlations whose selections are certified against FP64, FP32 Cholesky
+ * factors refined to FP64 accuracy. */
 typedef enum { CS_FP32 = 0, CS_BF16 = 1, CS_FP8_E4M3 = 2 } cs_precision;
 
 /* Options shared by the recovery calls; pass NULL for the defaults. */
@@ -67,7 +75,8 @@ typedef struct {
   double mu;               /* BIHT gradient step (Algorithm 4); default 0.1 (Section III) */
   int32_t *iters_out;      /* optional, device, P entries: iterations each pixel ran */
   uint8_t *converged_out;  /* optional, device, P entries: 1 if Delta < eps was reached,
-                              0 if the cap stopped it, 2 if its support LS failed */
+                              0 if the cap stopped it, 2 if its support LS failed, 3 (greedy
+                              calls) if its measurements are not finite */
   const int16_t *kappa_per_pixel; /* optional, device, P entries: per-pixel sparsity
                                      for the greedy calls; the call's kappa is then
                                      their upper bound and values outside 0..kappa
@@ -128,8 +137,11 @@ cs_status cs_measure(cs_ctx *ctx, const float *X, float *Y, const float *E, int6
  *   x = soft(z - A^T(A z - y)/L, lambda/L), t' = (1 + sqrt(1 + 4t^2))/2,
  *   z = x + ((t-1)/t')(x - x_prev), Delta = ||A x - A x_prev||;
  * until Delta < opts->eps or `iters` iterations.  lambda >= 0, iters >= 0.
- * prec = CS_BF16 runs A^T(A z - y) on the tensor cores with A z recomputed in FP32
- * accuracy (split operands) and A^T applied to the small residual in BF16. */
+ * prec = CS_BF16 runs both products on the tensor cores with split-BF16 operands for
+ * N and M (each padded to 16) of (128, 48), (208, 80), (224, 96) and (256, 112), i.e.
+ * N = 113..128 with M = 33..48 up to N = 241..256 with M = 97..112; it multiplies the
+ * increment x - x_prev and carries A x - y in FP32, so the products' rounding is
+ * relative to the increment.  Other shapes, and complex contexts, run the FP32 path. */
 cs_status cs_recover_fista(cs_ctx *ctx, const float *Y, float *X, int64_t P, double lambda,
                            int iters, const cs_opts *opts);
 
@@ -164,6 +176,11 @@ cs_status cs_recover_biht(cs_ctx *ctx, const float *Y, float *X, int64_t P, int 
 cs_status cs_recover_cosamp(cs_ctx *ctx, const float *Y, float *X, int64_t P, int kappa,
                             const cs_opts *opts);
 
+/* The arithmetic the last recovery call on this context computed its products in:
+ * CS_BF16 when FISTA or ADMM ran on the tensor cores, CS_FP32 otherwise (the FP32 SIMT
+ * path, or a greedy call).  Set when the call is queued. */
+cs_status cs_get_last_precision(const cs_ctx *ctx, cs_precision *prec);
+
 /* Algorithmic work of the last greedy call on this context (cs_recover_gomp, _biht,
  * _cosamp), in flops: per pixel and iteration the correlation A^T r (2MN), a Cholesky
  * least-squares solve on the support of n atoms (n^3/3 + 2n^2; the minimum-norm form
@@ -179,15 +196,17 @@ cs_status cs_get_work(cs_ctx *ctx, double *flops);
  * It needs no context and allocates nothing: the caller passes the FP64 dictionary
  * A_dev (M x N, row-major, e.g. from cs_get_dictionary) and the cube Y, X, all in
  * device memory it owns (host memory is rejected: staging it would allocate).  The
- * FP32/transposed copies of A, the FP64 Gram matrix and the kernel's work counter live
- * in one static device array of 1 MiB that every GPU loading the library holds until
- * exit; M x N shapes needing more (16 M N + 8 N^2 bytes plus alignment, e.g. M = 128
- * with N = 256) return CS_ERR_SHAPE.  The first call on a device looks up that array's
- * address; make it before any stream capture.  Every call re-derives the scratch
- * contents and resets the counter, and all calls share the one array: calls that
- * overlap on the GPU race and must be ordered by the caller.  Asynchronous on `stream`;
- * device-side conditions are reported only through opts->converged_out (2 = LS failure).
- * The paper has no counterpart of this entry point. */
+ * FP32 and FP64 copies of A^T, the FP32 copy of A, the Gram matrix A^T A in FP32 and
+ * FP64 and the kernel's work counter live in one static device array of 2 MiB that
+ * every GPU loading the library holds until exit; a shape needing more (20 M N + 12 N^2
+ * bytes plus alignment) returns CS_ERR_SHAPE, but every shape the library accepts
+ * (M <= 128, N <= 256) fits.  The first call on a device looks up that array's address;
+ * make it before any stream capture.  Every call re-derives the scratch contents and
+ * resets the counter, and all calls share the one array: calls that overlap on the GPU
+ * race and must be ordered by the caller.  Asynchronous on `stream`; no status word
+ * reaches the caller, so device-side conditions are reported only through
+ * opts->converged_out (2 = LS failure, 3 = measurements not finite).  Options are
+ * checked as in cs_recover_gomp.  The paper has no counterpart of this entry point. */
 cs_status cs_recover_gomp_noalloc(const double *A_dev, int M, int N, const float *Y, float *X,
                                   int64_t P, int kappa, int G, const cs_opts *opts,
                                   void *stream);

@@ -21,7 +21,8 @@ CS_FP32, CS_BF16, CS_FP8_E4M3 = 0, 1, 2
 
 EXPORTED = ["cs_opts_default", "cs_create", "cs_destroy", "cs_get_lipschitz", "cs_get_dictionary",
             "cs_measure", "cs_recover_fista", "cs_recover_admm", "cs_recover_gomp",
-            "cs_recover_biht", "cs_recover_cosamp", "cs_get_work", "cs_recover_gomp_noalloc",
+            "cs_recover_biht", "cs_recover_cosamp", "cs_get_work", "cs_get_last_precision",
+            "cs_recover_gomp_noalloc",
             "cs_recover_batch", "cs_recover_stream", "cs_sparsify", "cs_create_complex",
             "cs_sync", "cs_last_error"]
 CS_ALGO_FISTA, CS_ALGO_ADMM, CS_ALGO_GOMP, CS_ALGO_BIHT, CS_ALGO_COSAMP = 0, 1, 2, 3, 4
@@ -80,6 +81,7 @@ def load_library(path: str = LIB_PATH):
     lib.cs_recover_biht.argtypes = [vp, vp, vp, i64, i32, op]
     lib.cs_recover_cosamp.argtypes = [vp, vp, vp, i64, i32, op]
     lib.cs_get_work.argtypes = [vp, ctypes.POINTER(dbl)]
+    lib.cs_get_last_precision.argtypes = [vp, ctypes.POINTER(i32)]
     lib.cs_recover_gomp_noalloc.argtypes = [vp, i32, i32, vp, vp, i64, i32, i32, op, vp]
     lib.cs_recover_batch.argtypes = [ctypes.POINTER(cs_batch_item), i32, i32,
                                      ctypes.POINTER(cs_algo_params), op]
@@ -316,6 +318,14 @@ def cs_recover_cosamp(ctx: Context, Y, X, kappa, opts: cs_opts | None = None, P=
                                             int(P), int(kappa),
                                             ctypes.byref(opts) if opts else None))
     return X
+
+
+def cs_get_last_precision(ctx: Context) -> str:
+    """The arithmetic of the last recovery call's products: "bf16" (split-BF16 tensor
+    cores) or "fp32"."""
+    v = ctypes.c_int32(0)
+    _check(load_library().cs_get_last_precision(ctx.handle, ctypes.byref(v)))
+    return {CS_FP32: "fp32", CS_BF16: "bf16"}.get(v.value, str(v.value))
 
 
 def cs_get_work(ctx: Context) -> float:

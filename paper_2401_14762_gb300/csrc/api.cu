@@ -143,8 +143,9 @@ cs_status check_ctx(const cs_ctx* ctx) {
 cs_status check_opts(const cs_opts& o) {
   if (!(o.eps >= 0.0) || !std::isfinite(o.eps)) return arg_error("eps must be >= 0");
   if (o.max_iters < 0) return arg_error("max_iters < 0");
-  if (o.prec != CS_FP32 && o.prec != CS_BF16 && o.prec != CS_FP8_E4M3)
-    return arg_error("unknown precision");
+  if (o.prec == CS_FP8_E4M3)
+    return arg_error("CS_FP8_E4M3 is not offered: E4M3 products do not meet rel-L2 1e-3");
+  if (o.prec != CS_FP32 && o.prec != CS_BF16) return arg_error("unknown precision");
   if ((o.iters_out && !is_device_ptr(o.iters_out)) ||
       (o.converged_out && !is_device_ptr(o.converged_out)) ||
       (o.kappa_per_pixel && !is_device_ptr(o.kappa_per_pixel)))
@@ -712,6 +713,13 @@ cs_status cs_recover_gomp_noalloc(const double* A_dev, int M, int N, const float
                    o.iters_out, o.converged_out, o.prec, o.cycle_skip != 0};
   e = cs::launch_gomp_noalloc(A_dev, M, N, a, static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_fail(e, "cs_recover_gomp_noalloc");
+  return CS_OK;
+}
+
+cs_status cs_get_last_precision(const cs_ctx* ctx, cs_precision* prec) {
+  if (cs_status s = cs::check_ctx(ctx)) return s;
+  if (!prec) return arg_error("prec is NULL");
+  *prec = ctx->c.last_prec;
   return CS_OK;
 }
 

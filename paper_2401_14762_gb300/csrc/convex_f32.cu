@@ -572,8 +572,11 @@ cudaError_t launch_fista(Ctx& c, const ConvexArgs& a, bool table) {
     cudaError_t e = momentum_table(c, a.iters);
     if (e != cudaSuccess) return e;
   }
-  if (a.prec != CS_FP32 && !c.complex_pairs && fista_tc_supported(c.M, c.N))
+  if (a.prec != CS_FP32 && !c.complex_pairs && fista_tc_supported(c.M, c.N)) {
+    c.last_prec = CS_BF16;
     return launch_fista_tc(c, a);
+  }
+  c.last_prec = CS_FP32;
   CvParams p = base_params(c);
   p.beta = c.beta;
   p.Y = a.Y;
@@ -591,9 +594,12 @@ cudaError_t launch_fista(Ctx& c, const ConvexArgs& a, bool table) {
   CS_DISPATCH_MR_NCH(fista_mr, c, p, blocks);
 }
 
-cudaError_t launch_admm(const Ctx& c, const ConvexArgs& a) {
-  if (a.P > 0 && a.prec != CS_FP32 && !c.complex_pairs && admm_tc_supported(c.M, c.N))
+cudaError_t launch_admm(Ctx& c, const ConvexArgs& a) {
+  if (a.P > 0 && a.prec != CS_FP32 && !c.complex_pairs && admm_tc_supported(c.M, c.N)) {
+    c.last_prec = CS_BF16;
     return launch_admm_tc(c, a);
+  }
+  c.last_prec = CS_FP32;
   CvParams p = base_params(c);
   p.Y = a.Y;
   p.X = a.X;

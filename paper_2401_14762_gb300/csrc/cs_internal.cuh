@@ -35,6 +35,7 @@ struct Ctx {
   // complex values as (re, im) pairs; FISTA's and ADMM's thresholds act on the moduli
   bool complex_pairs = false;
   cudaStream_t stream = nullptr;
+  cs_precision last_prec = CS_FP32;  // the arithmetic of the last recovery call's products
   double L = 0.0;             // Lipschitz constant lambda_max(A^T A)
   double* A64 = nullptr;      // M x N, FP64
   double* At64 = nullptr;     // N x M, FP64 (column j of A contiguous)
@@ -111,7 +112,7 @@ cudaError_t momentum_table(Ctx& c, int iters);
 cudaError_t launch_fista(Ctx& c, const ConvexArgs& a, bool table = true);
 bool fista_tc_supported(int M, int N);
 cudaError_t launch_fista_tc(const Ctx& c, const ConvexArgs& a);
-cudaError_t launch_admm(const Ctx& c, const ConvexArgs& a);
+cudaError_t launch_admm(Ctx& c, const ConvexArgs& a);
 bool admm_tc_supported(int M, int N);
 cudaError_t launch_admm_tc(const Ctx& c, const ConvexArgs& a);
 

@@ -1554,6 +1554,7 @@ cudaError_t run_greedy(Ctx& c, GreedyAlgo algo, const GreedyArgs& a, const GrCub
 }  // namespace
 
 cudaError_t launch_greedy(Ctx& c, GreedyAlgo algo, const GreedyArgs& a) {
+  c.last_prec = CS_FP32;
   if (a.P == 0) return cudaSuccess;
   GrCube cube = cube_of(c, a.Y, a.X, a.P, a.kappa_pp, a.iters_out, a.conv_out, 0);
   return run_greedy(c, algo, a, &cube, 1, c.M, c.N, a.P);

@@ -33,11 +33,29 @@ def test_fista_bf16_powerlaw(cs, shape, kind, iters, P):
     ctx = cs.cs_create(M, N, Phi=pr.Phi)
     Xb, it, cv = gpu_run(cs.cs_recover_fista, ctx, pr.Y, N, 1e-3, iters, eps=0.0,
                          prec=cs.CS_BF16)
+    assert cs.cs_get_last_precision(ctx) == "bf16"  # the tensor-core path ran
     Xf, _, _ = gpu_run(cs.cs_recover_fista, ctx, pr.Y, N, 1e-3, iters, eps=0.0)
+    assert cs.cs_get_last_precision(ctx) == "fp32"
     err, err32 = rel_l2(Xb, Xo), rel_l2(Xf, Xo)
     print(f"bf16 {err:.2e} fp32 {err32:.2e}")
     assert np.all(it == iters) and np.all(cv == 0)
     assert err <= REL_L2_MIXED
+
+
+def test_fp8_is_rejected_and_untiled_shapes_report_fp32(cs):
+    """E4M3 products are not offered (they miss the 1e-3 bar by far); a BF16 request on a
+    shape without a tensor-core tile runs, and reports, the FP32 path."""
+    pr = Problem(64, 128, 40, "powerlaw", seed=2, noise_var=1e-3)
+    ctx = cs.cs_create(pr.M, pr.N, Phi=pr.Phi, admm_rho=1.0)
+    for call, args in ((cs.cs_recover_fista, (1e-3, 20)), (cs.cs_recover_admm, (1.0, 1e-3, 20)),
+                       (cs.cs_recover_gomp, (8, 2))):
+        with pytest.raises(cs.CsError) as e:
+            gpu_run(call, ctx, pr.Y, pr.N, *args, prec=cs.CS_FP8_E4M3)
+        assert e.value.status == cs.CS_ERR_ARG
+    Xo, _ = orc.fista(pr.A, pr.Y, pr.L, 1e-3, 0.0, 20)
+    Xb, _, _ = gpu_run(cs.cs_recover_fista, ctx, pr.Y, pr.N, 1e-3, 20, eps=0.0, prec=cs.CS_BF16)
+    assert cs.cs_get_last_precision(ctx) == "fp32"   # M = 64 pads to 64: no tile
+    assert rel_l2(Xb, Xo) <= REL_L2_MIXED
 
 
 def test_fista_bf16_small_sparse(cs):

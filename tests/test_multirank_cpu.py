@@ -55,6 +55,6 @@ def test_two_gloo_ranks():
     import bench
     for rank, t, value, seeds, printed in res:
         assert t == 150.0                                # the slowest rank's time
-        assert value == pytest.approx(bench.P * 5 * 2 / 0.150)
+        assert value == pytest.approx(bench.P * len(bench.STEP_ALGOS) * 2 / 0.150)
         assert seeds[0] != seeds[1]                      # each rank its own cube
         assert printed == ""
