@@ -135,7 +135,8 @@ template <int NP, int MP>
 __global__ void __launch_bounds__(kTcThreads, 1) k_fista_tc(FtcParams p) {
   using S = Shape<NP, MP>;
   extern __shared__ __align__(1024) unsigned char sm[];
-  __shared__ __align__(8) uint64_t mb[4];  // GEMM2 half 0, half 1, GEMM1 first chunks, GEMM1
+  __shared__ __align__(8) uint64_t mb[5];  // GEMM2 half 0, half 1, GEMM1 first chunks, GEMM1,
+                                           // and the drain after a failed wait
   __shared__ uint32_t tmem_slot;
   __shared__ int s_fail;  // a bounded wait ran out (set by any thread, read after a barrier)
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -155,7 +156,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_fista_tc(FtcParams p) {
   // MP x NP: GEMM1 reads it K-major (A^T), GEMM2 MN-major
   tc::stage_split(p.A64, M, N, MP, NP, sAh, sAl);
   if (tid == 0) {
-    for (int k = 0; k < 4; ++k) tc::mbar_init(&mb[k], 1);
+    for (int k = 0; k < 5; ++k) tc::mbar_init(&mb[k], 1);
     s_fail = 0;
   }
   if (warp == 0) tc::tmem_alloc(&tmem_slot, S::TCOLS);
@@ -206,7 +207,6 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_fista_tc(FtcParams p) {
   uint32_t ph = 0;   // phase parity of the four mbarriers in this iteration
   int ui = 0;        // region holding D (T0 = columns [0, RW), T1 = [RW, 2 RW))
   bool failed = false;
-  bool ran = false;  // an iteration's products were committed (GEMM1's last on mb[3])
 
   for (int i = 1;; ++i) {
     const uint32_t tU = tl + ui * S::RW, tO = tl + (1 - ui) * S::RW;
@@ -371,7 +371,6 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_fista_tc(FtcParams p) {
         }
       }
     }
-    ran = true;
     failed |= !tc::mbar_wait(&mb[3], ph, kWaitLimitNs);
     tc::fence_after_sync();
     ph ^= 1u;
@@ -379,10 +378,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_fista_tc(FtcParams p) {
     beta_prev = beta;
   }
   if (__syncthreads_or(failed)) {
-    // a product never completed: report, give the last iteration's final commit one more
-    // bounded wait (its completion implies every earlier MMA's), then release TMEM
-    if (tid == 0) atomicOr(p.status, kStTimeout);
-    if (ran) tc::mbar_wait(&mb[3], ph ^ 1u, kWaitLimitNs);
+    // a product never completed: report, then one commit that tracks every MMA thread 0
+    // issued gets a last bounded wait before TMEM is released
+    if (tid == 0) {
+      atomicOr(p.status, kStTimeout);
+      tc::mma_commit(&mb[4]);
+    }
+    tc::mbar_wait(&mb[4], 0, kWaitLimitNs);
   }
   tc::fence_before_sync();
   __syncthreads();

@@ -107,12 +107,12 @@ def test_fista_bf16_stop_rule_and_edges(cs):
 
 # --------------------------------------------------------------------------- ADMM
 # prec = CS_BF16 runs ADMM's three products (A d, W e, A^T h) on the tensor cores with
-# split-BF16 operands where the tile fits in shared memory (N = 120 and 200 here); other
-# shapes run the FP32 path, which must meet the same bar.
+# split-BF16 operands for the four tile shapes (N = 120, 200, 224, 256 with M = 0.4 N).
 @pytest.mark.parametrize("shape,P,rho", [((80, 200), 32 * 20 + 7, 1.0),
                                          ((48, 120), 300, 1.0),
                                          ((48, 120), 300, 0.5),
-                                         ((90, 224), 200, 1.0)])
+                                         ((90, 224), 200, 1.0),
+                                         ((102, 256), 128 * 2 + 9, 1.0)])
 def test_admm_bf16_powerlaw(cs, shape, P, rho):
     M, N = shape
     pr = Problem(M, N, P, "powerlaw", seed=3, noise_var=1e-3)
@@ -120,13 +120,12 @@ def test_admm_bf16_powerlaw(cs, shape, P, rho):
     ctx = cs.cs_create(M, N, Phi=pr.Phi, admm_rho=rho)
     Xb, it, cv = gpu_run(cs.cs_recover_admm, ctx, pr.Y, N, rho, 1e-3, 300, eps=0.0,
                          prec=cs.CS_BF16)
+    assert cs.cs_get_last_precision(ctx) == "bf16"  # the tensor-core path ran
     Xf, _, _ = gpu_run(cs.cs_recover_admm, ctx, pr.Y, N, rho, 1e-3, 300, eps=0.0)
     err, err32 = rel_l2(Xb, Xo), rel_l2(Xf, Xo)
     print(f"admm bf16 {err:.2e} fp32 {err32:.2e}")
     assert np.all(it == 300) and np.all(cv == 0)
     assert err <= REL_L2_MIXED
-    if N in (120, 200):
-        assert not np.array_equal(Xb, Xf)  # the tensor-core path ran
 
 
 def test_admm_bf16_converged(cs):
