@@ -314,6 +314,10 @@ def run_gpu(args):
             "fista": cs.make_opts(eps=EPS, prec=cs.CS_BF16, iters_out=iters["fista"],
                                   converged_out=conv["fista"])}
     work = {}
+    # the autotuner picks gOMP's launch configuration on a sample of this cube
+    cs.cs_measure(ctx, Xt, Y, E)
+    tune_step = cs.cs_autotune(ctx, cs.CS_ALGO_GOMP, Y[:65536], KAPPA, G,
+                               cs.make_opts(eps=EPS))
 
     def step(ev=None):
         def mark(k):
@@ -522,6 +526,7 @@ def run_gpu(args):
                 "clocks": clk.summary(),
                 "kernels": kernels,
                 "arms": arms,
+                "autotune_gomp": tune_step,
                 "accuracy_rel_l2_vs_oracle": acc,
                 "psnr_vs_truth": psnr,
                 "table1": table1,
@@ -540,6 +545,7 @@ def run_gpu(args):
         line["sparsify"] = run_sparsify(cs, sy, sub[0], dev, stream)
         del sub
         line["cube_1024x1024x224"] = run_context_cube(cs, sy, dev, stream)
+        line["autotune"] = run_autotune(cs, sy, dev)
         if not args.no_batch:
             line["batch"] = run_batch(cs, sy, dev, stream)
         print(json.dumps(line), flush=True)
@@ -577,12 +583,19 @@ def run_context_cube(cs, sy, dev, stream):
         "cosamp": lambda Yv, Xv: cs.cs_recover_cosamp(ctx, Yv, Xv, kap, plain),
     }
     res = {}
+    tuned = {}
+    for a, code in (("gomp", cs.CS_ALGO_GOMP), ("biht", cs.CS_ALGO_BIHT),
+                    ("cosamp", cs.CS_ALGO_COSAMP)):
+        tuned[a] = cs.cs_autotune(ctx, code, Y[:65536], kap, G_ if a == "gomp" else 0,
+                                  cs.make_opts(eps=EPS, mu=MU))
     for a, call in calls.items():
         call(Y[:4096], X[:4096])
         ms = timed(stream, lambda: call(Y, X), flush)
         cs.cs_sync(ctx)
         res[a] = {"ms": ms, "spectra_per_s": P_ / (ms * 1e-3),
                   "path": cs.cs_get_last_precision(ctx)}
+        if a in tuned:
+            res[a]["launch"] = tuned[a]
     # accuracy on the oracle's own measurements of 1024 pixels
     n_s = 1024
     A = orc.dictionary(Phi)
@@ -605,6 +618,33 @@ def run_context_cube(cs, sy, dev, stream):
             "pixels": P_, "algorithms": res,
             "accuracy_sample": f"{n_s} pixels, FP64 oracle on the host ({secs:.1f} s)",
             "l2": "flushed before each timed run"}
+
+
+def run_autotune(cs, sy, dev):
+    """The autotuner on the three cube shapes (512 x 512 x 200, M = 80; 1024 x 1024 x 224,
+    M = 90; 2048 x 2048 x 256, M = 102): the greedy kernels' launch configuration chosen
+    on a 65,536-pixel sample of each, and its time against the built-in choice's."""
+    import torch
+    out = {}
+    for name, (M_, N_, kap) in {"512x512x200": (80, 200, 20), "1024x1024x224": (90, 224, 20),
+                                "2048x2048x256": (M, N, KAPPA)}.items():
+        n = 65536
+        Phi = sy.gaussian_phi(M_, N_, SEED)
+        ctx = cs.cs_create(M_, N_, Phi=Phi, stream=torch.cuda.current_stream().cuda_stream)
+        Xt = sy.powerlaw_coeffs_torch(n, N_, SEED, dev)
+        E = sy.noise_torch(n, M_, NOISE_VAR, SEED, dev)
+        Y = torch.empty((n, M_), device=dev)
+        cs.cs_measure(ctx, Xt, Y, E)
+        rec = {}
+        for a, code in (("gomp", cs.CS_ALGO_GOMP), ("biht", cs.CS_ALGO_BIHT),
+                        ("cosamp", cs.CS_ALGO_COSAMP)):
+            t = cs.cs_autotune(ctx, code, Y, kap, G if a == "gomp" else 0,
+                               cs.make_opts(eps=EPS, mu=MU))
+            t["gain"] = t["ms_default"] / t["ms"]
+            rec[a] = t
+        out[name] = rec
+        cs.cs_destroy(ctx)
+    return out
 
 
 def run_pushbroom(cs, ctx, Yh, outh, lines=64):

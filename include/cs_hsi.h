@@ -265,6 +265,37 @@ typedef struct {
 cs_status cs_recover_batch(const cs_batch_item *items, int n_items, cs_algo algo,
                            const cs_algo_params *params, const cs_opts *opts);
 
+/* ---- Autotuning of the greedy kernels' launch configuration ---- */
+
+/* A launch configuration of the greedy kernel (one warp per pixel, persistent). */
+typedef struct {
+  int factor_rows;   /* gOMP: rows of its FP32 Cholesky factor kept in shared memory (a
+                        support that outgrows them is solved in FP64 in global memory);
+                        BIHT and CoSaMP keep their whole support */
+  int warps_per_cta; /* the CTAs per SM follow from the shared memory they take */
+  double ms;         /* time on the tuning sample with this configuration */
+  double ms_default; /* time on the sample with the built-in choice */
+  int tuned;         /* 1 if this configuration replaced the built-in one */
+} cs_tuning;
+
+/* Measures the greedy kernel's launch configurations -- factor capacity (gOMP, from
+ * 2 kappa to the whole support in steps of 8) x warps per CTA (2..8, as shared memory
+ * allows) -- on a sample of the caller's cube (Y_dev: P x M device measurements; a few
+ * tens of thousands of pixels suffice), with CUDA events on the context's stream, and
+ * keeps the fastest for later calls of `algo` (gOMP, BIHT or CoSaMP) with the same kappa
+ * and G on this context, unless none beats the built-in choice.  Results do not depend
+ * on the configuration (every pixel computes the same iterates).  Writes the outcome to
+ * *out.  Blocks until the measurements are done.  CS_ERR_ARG for FISTA/ADMM: their tile
+ * is fixed by the 128 TMEM lanes and the shared memory a shape takes. */
+cs_status cs_autotune(cs_ctx *ctx, cs_algo algo, const cs_algo_params *params, const float *Y_dev,
+                      int64_t P, const cs_opts *opts, cs_tuning *out);
+
+/* Installs a configuration (for example one cs_autotune chose earlier and the caller
+ * cached) for later calls of `algo` with params->kappa and params->G; t == NULL or
+ * t->tuned == 0 restores the built-in choice. */
+cs_status cs_set_tuning(cs_ctx *ctx, cs_algo algo, const cs_algo_params *params,
+                        const cs_tuning *t);
+
 /* Pushbroom streaming (Section II: a pushbroom sensor delivers a frame of pixels at a
  * time, and per-pixel recovery needs none of the rest of the cube).  Recovers a cube
  * held in HOST memory (Y: P x M, X: P x N, row-major; pinned memory lets the copies

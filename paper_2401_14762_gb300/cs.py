@@ -22,6 +22,7 @@ CS_FP32, CS_BF16, CS_FP8_E4M3 = 0, 1, 2
 EXPORTED = ["cs_opts_default", "cs_create", "cs_destroy", "cs_get_lipschitz", "cs_get_dictionary",
             "cs_measure", "cs_recover_fista", "cs_recover_admm", "cs_recover_gomp",
             "cs_recover_biht", "cs_recover_cosamp", "cs_get_work", "cs_get_last_precision",
+            "cs_autotune", "cs_set_tuning",
             "cs_recover_gomp_noalloc",
             "cs_recover_batch", "cs_recover_stream", "cs_sparsify", "cs_create_complex",
             "cs_sync", "cs_last_error"]
@@ -43,6 +44,12 @@ class cs_batch_item(ctypes.Structure):
 class cs_algo_params(ctypes.Structure):
     _fields_ = [("lambda_", ctypes.c_double), ("rho", ctypes.c_double), ("iters", ctypes.c_int),
                 ("kappa", ctypes.c_int), ("G", ctypes.c_int)]
+
+
+class cs_tuning(ctypes.Structure):
+    _fields_ = [("factor_rows", ctypes.c_int), ("warps_per_cta", ctypes.c_int),
+                ("ms", ctypes.c_double), ("ms_default", ctypes.c_double),
+                ("tuned", ctypes.c_int)]
 
 
 class cs_opts(ctypes.Structure):
@@ -82,6 +89,10 @@ def load_library(path: str = LIB_PATH):
     lib.cs_recover_cosamp.argtypes = [vp, vp, vp, i64, i32, op]
     lib.cs_get_work.argtypes = [vp, ctypes.POINTER(dbl)]
     lib.cs_get_last_precision.argtypes = [vp, ctypes.POINTER(i32)]
+    lib.cs_autotune.argtypes = [vp, i32, ctypes.POINTER(cs_algo_params), vp, i64,
+                                ctypes.POINTER(cs_opts), ctypes.POINTER(cs_tuning)]
+    lib.cs_set_tuning.argtypes = [vp, i32, ctypes.POINTER(cs_algo_params),
+                                  ctypes.POINTER(cs_tuning)]
     lib.cs_recover_gomp_noalloc.argtypes = [vp, i32, i32, vp, vp, i64, i32, i32, op, vp]
     lib.cs_recover_batch.argtypes = [ctypes.POINTER(cs_batch_item), i32, i32,
                                      ctypes.POINTER(cs_algo_params), op]
@@ -318,6 +329,53 @@ def cs_recover_cosamp(ctx: Context, Y, X, kappa, opts: cs_opts | None = None, P=
                                             int(P), int(kappa),
                                             ctypes.byref(opts) if opts else None))
     return X
+
+
+def cs_autotune(ctx: Context, algo: int, Y, kappa: int, G: int = 0,
+                opts: cs_opts | None = None, cache: str | None = None, P=None) -> dict:
+    """Chooses the greedy kernel's launch configuration for (algo, kappa, G) on this
+    context by timing the candidates on the sample Y (device, P x M); later calls with
+    the same parameters use it.  With `cache` (a JSON file path) a configuration chosen
+    before for the same device, algorithm, M x N, kappa and G is installed instead of
+    measured, and a new choice is added to the file."""
+    import json
+    lib = load_library()
+    prm = cs_algo_params(0.0, 0.0, 0, int(kappa), int(G))
+    key = None
+    if cache:
+        try:
+            import torch
+            dev = torch.cuda.get_device_name()
+        except Exception:
+            dev = "cuda"
+        key = f"{dev}|algo{algo}|{ctx.M}x{ctx.N}|kappa{kappa}|G{G}"
+        try:
+            with open(cache) as f:
+                rec = json.load(f).get(key)
+        except (OSError, ValueError):
+            rec = None
+        if rec:
+            t = cs_tuning(rec["factor_rows"], rec["warps_per_cta"], rec["ms"],
+                          rec["ms_default"], rec["tuned"])
+            _check(lib.cs_set_tuning(ctx.handle, int(algo), ctypes.byref(prm), ctypes.byref(t)))
+            return dict(rec, cached=True)
+    n = int(P if P is not None else Y.shape[0])
+    t = cs_tuning()
+    o = opts if opts is not None else cs_opts_default()
+    _check(lib.cs_autotune(ctx.handle, int(algo), ctypes.byref(prm), _ptr(Y, np.float32), n,
+                           ctypes.byref(o), ctypes.byref(t)))
+    rec = {"factor_rows": t.factor_rows, "warps_per_cta": t.warps_per_cta, "ms": t.ms,
+           "ms_default": t.ms_default, "tuned": t.tuned, "sample_pixels": n}
+    if cache:
+        try:
+            with open(cache) as f:
+                allrec = json.load(f)
+        except (OSError, ValueError):
+            allrec = {}
+        allrec[key] = rec
+        with open(cache, "w") as f:
+            json.dump(allrec, f, indent=1, sort_keys=True)
+    return dict(rec, cached=False)
 
 
 def cs_get_last_precision(ctx: Context) -> str:

@@ -716,6 +716,69 @@ cs_status cs_recover_gomp_noalloc(const double* A_dev, int M, int N, const float
   return CS_OK;
 }
 
+cs_status cs_autotune(cs_ctx* ctx, cs_algo algo, const cs_algo_params* params,
+                      const float* Y_dev, int64_t P, const cs_opts* opts, cs_tuning* out) {
+  cs::set_error("");
+  if (cs_status s = cs::check_ctx(ctx)) return s;
+  if (!params || !out) return arg_error("params or out is NULL");
+  if (algo != CS_ALGO_GOMP && algo != CS_ALGO_BIHT && algo != CS_ALGO_COSAMP)
+    return arg_error("only the greedy algorithms have launch configurations to tune");
+  cs_opts o;
+  cs_opts_default(&o);
+  if (opts) o = *opts;
+  o.iters_out = nullptr;
+  o.converged_out = nullptr;
+  o.kappa_per_pixel = nullptr;
+  if (cs_status s = cs::check_opts(o)) return s;
+  cs::Ctx& c = ctx->c;
+  if (c.complex_pairs) return arg_error("complex contexts support FISTA and ADMM only");
+  if (P < 1 || !Y_dev || !cs::is_device_ptr(Y_dev))
+    return arg_error("the tuning sample must be P >= 1 pixels in device memory");
+  const int kappa = params->kappa, G = algo == CS_ALGO_GOMP ? params->G : 0;
+  if (kappa < 0 || kappa > c.N) return arg_error("kappa out of range");
+  if (algo == CS_ALGO_COSAMP && 2 * kappa > c.N) return arg_error("CoSaMP needs 2 kappa <= N");
+  if (algo == CS_ALGO_GOMP && (G < 1 || G > c.N)) return arg_error("G must be in 1..N");
+  cudaError_t e = cs::ensure_stage(&c.stage_out, &c.stage_out_bytes,
+                                   sizeof(float) * (size_t)P * c.N);
+  if (e != cudaSuccess) return cuda_fail(e, "tuning output buffer");
+  const cs::GreedyAlgo ga =
+      algo == CS_ALGO_GOMP ? cs::kGomp : (algo == CS_ALGO_BIHT ? cs::kBiht : cs::kCosamp);
+  cs::GreedyArgs a{Y_dev, c.stage_out, P, kappa, G, o.mu, o.eps, o.max_iters, nullptr, kappa,
+                   nullptr, nullptr, o.prec, o.cycle_skip != 0};
+  cs::GreedyTune t;
+  e = cs::tune_greedy(c, ga, a, &t);
+  if (e != cudaSuccess) return cuda_fail(e, "cs_autotune");
+  out->factor_rows = t.d32;
+  out->warps_per_cta = t.warps;
+  out->ms = t.ms;
+  out->ms_default = t.ms_default;
+  out->tuned = t.valid ? 1 : 0;
+  return CS_OK;
+}
+
+cs_status cs_set_tuning(cs_ctx* ctx, cs_algo algo, const cs_algo_params* params,
+                        const cs_tuning* t) {
+  if (cs_status s = cs::check_ctx(ctx)) return s;
+  if (!params) return arg_error("params is NULL");
+  if (algo != CS_ALGO_GOMP && algo != CS_ALGO_BIHT && algo != CS_ALGO_COSAMP)
+    return arg_error("only the greedy algorithms have launch configurations to tune");
+  const int k = algo == CS_ALGO_GOMP ? 0 : (algo == CS_ALGO_BIHT ? 1 : 2);
+  cs::GreedyTune g;
+  if (t && t->tuned) {
+    if (t->warps_per_cta < 1 || t->warps_per_cta > 8 || t->factor_rows < 0)
+      return arg_error("warps_per_cta must be in 1..8 and factor_rows >= 0");
+    g.valid = true;
+    g.kappa = params->kappa;
+    g.G = algo == CS_ALGO_GOMP ? params->G : 0;
+    g.d32 = t->factor_rows;
+    g.warps = t->warps_per_cta;
+    g.ms = t->ms;
+    g.ms_default = t->ms_default;
+  }
+  ctx->c.tune[k] = g;
+  return CS_OK;
+}
+
 cs_status cs_get_last_precision(const cs_ctx* ctx, cs_precision* prec) {
   if (cs_status s = cs::check_ctx(ctx)) return s;
   if (!prec) return arg_error("prec is NULL");

@@ -29,8 +29,20 @@ inline int smem_ld(int n) {
   return ld;
 }
 
+// A launch configuration of the greedy kernel measured best by the autotuner
+// (cs_autotune) for one algorithm and its (kappa bound, G): the rows of the FP32 factor
+// kept in shared memory (gOMP; the others need their whole support) and the warps per
+// CTA (the CTAs per SM follow from the shared memory they take).
+struct GreedyTune {
+  bool valid = false;
+  int kappa = 0, G = 0;
+  int d32 = 0, warps = 0;
+  double ms = 0.0, ms_default = 0.0;
+};
+
 struct Ctx {
   int M = 0, N = 0, device = 0, num_sms = 0;
+  GreedyTune tune[3];  // per greedy algorithm (gOMP, BIHT, CoSaMP)
   // cs_create_complex: A is the real form of a complex dictionary and every vector holds
   // complex values as (re, im) pairs; FISTA's and ADMM's thresholds act on the moduli
   bool complex_pairs = false;
@@ -135,6 +147,9 @@ struct GreedyArgs {
   bool cycle_skip;  // BIHT/CoSaMP: stop at a repeated iterate (exact, see k_greedy)
 };
 cudaError_t launch_greedy(Ctx& c, GreedyAlgo algo, const GreedyArgs& a);
+// Times the kernel's launch configurations on the sample a.Y (a.X receives its output)
+// and keeps the fastest in c.tune[algo]; *out gets it and the default's time.
+cudaError_t tune_greedy(Ctx& c, GreedyAlgo algo, const GreedyArgs& a, GreedyTune* out);
 // One cube of a batched greedy launch (device pointers; Y/X/kappa/iters/conv per cube).
 struct GreedyCube {
   const Ctx* ctx;

@@ -1505,6 +1505,13 @@ cudaError_t run_greedy(Ctx& c, GreedyAlgo algo, const GreedyArgs& a, const GrCub
       --d;
     p.d32 = d > lo ? d : lo;
   }
+  // a configuration the autotuner chose for this call's parameters (single cubes)
+  const GreedyTune& tn = c.tune[algo];
+  const bool tuned = n == 1 && tn.valid && tn.kappa == a.kappa_max && tn.G == a.G;
+  if (tuned && algo == kGomp) {
+    const int lo = 2 * p.kmax < p.dmax ? 2 * p.kmax : p.dmax;
+    p.d32 = tn.d32 < lo ? lo : (tn.d32 > p.dmax ? p.dmax : tn.d32);
+  }
   Layout lay(Mmax, Nmax, p.cmax, p.dmax, p.kmax, p.selmax, false, algo == kGomp,
              algo != kGomp, algo == kBiht, p.d32);
   p.warp_bytes = lay.total;
@@ -1513,6 +1520,8 @@ cudaError_t run_greedy(Ctx& c, GreedyAlgo algo, const GreedyArgs& a, const GrCub
   if (warps1 > 8) warps1 = 8;
   if (warps2 > 8) warps2 = 8;
   int warps = (warps2 >= 1 && 2 * warps2 >= warps1) ? warps2 : warps1;
+  if (tuned && tn.warps >= 1 && tn.warps <= 8 && (size_t)tn.warps * lay.total <= 220 * 1024)
+    warps = tn.warps;
   if (warps < 1) warps = 1;
   if ((size_t)warps * lay.total > 220 * 1024) return cudaErrorInvalidConfiguration;
   size_t smem = (size_t)warps * lay.total;
@@ -1558,6 +1567,72 @@ cudaError_t launch_greedy(Ctx& c, GreedyAlgo algo, const GreedyArgs& a) {
   if (a.P == 0) return cudaSuccess;
   GrCube cube = cube_of(c, a.Y, a.X, a.P, a.kappa_pp, a.iters_out, a.conv_out, 0);
   return run_greedy(c, algo, a, &cube, 1, c.M, c.N, a.P);
+}
+
+cudaError_t tune_greedy(Ctx& c, GreedyAlgo algo, const GreedyArgs& a, GreedyTune* out) {
+  if (a.P < 1) return cudaErrorInvalidValue;
+  GrParams p{};
+  capacities(p, algo, a, c.M, c.N);
+  const int lo = 2 * p.kmax < p.dmax ? 2 * p.kmax : p.dmax;
+  // candidate factor capacities (gOMP: from 2 kappa to the whole support in steps of 8;
+  // the others hold their whole support) and warps per CTA
+  std::vector<int> caps;
+  if (algo == kGomp) {
+    for (int d = lo; d < p.dmax; d += 8) caps.push_back(d);
+    caps.push_back(p.dmax);
+  } else {
+    caps.push_back(p.dmax);
+  }
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  auto timed = [&](float* ms) {
+    cudaError_t er = cudaEventRecord(e0, c.stream);
+    if (er == cudaSuccess) er = launch_greedy(c, algo, a);
+    if (er == cudaSuccess) er = cudaEventRecord(e1, c.stream);
+    if (er == cudaSuccess) er = cudaEventSynchronize(e1);
+    if (er == cudaSuccess) er = cudaEventElapsedTime(ms, e0, e1);
+    return er;
+  };
+  GreedyTune best;
+  float ms_def = 0.f;
+  c.tune[algo].valid = false;
+  if (e == cudaSuccess) e = launch_greedy(c, algo, a);  // warm-up (and workspace sizing)
+  if (e == cudaSuccess) e = timed(&ms_def);
+  for (size_t ic = 0; ic < caps.size() && e == cudaSuccess; ++ic) {
+    const Layout lay(c.M, c.N, p.cmax, p.dmax, p.kmax, p.selmax, false, algo == kGomp,
+                     algo != kGomp, algo == kBiht, caps[ic]);
+    for (int wp = 2; wp <= 8 && e == cudaSuccess; ++wp) {
+      if ((size_t)wp * lay.total > 220 * 1024) break;
+      GreedyTune t;
+      t.valid = true;
+      t.kappa = a.kappa_max;
+      t.G = a.G;
+      t.d32 = caps[ic];
+      t.warps = wp;
+      c.tune[algo] = t;
+      float ms = 0.f;
+      e = timed(&ms);
+      if (e == cudaSuccess && (!best.valid || ms < best.ms)) {
+        best = t;
+        best.ms = ms;
+      }
+    }
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (e != cudaSuccess) {
+    c.tune[algo].valid = false;
+    return e;
+  }
+  best.ms_default = ms_def;
+  // keep the default when no candidate beats it
+  if (!best.valid || best.ms >= ms_def) best.valid = false;
+  c.tune[algo] = best;
+  *out = best;
+  out->ms_default = ms_def;
+  if (!best.valid) out->ms = ms_def;
+  return cudaSuccess;
 }
 
 cudaError_t launch_greedy_batch(Ctx& c0, GreedyAlgo algo, const GreedyCube* cubes, int n,
