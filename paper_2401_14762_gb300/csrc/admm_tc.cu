@@ -47,6 +47,7 @@ struct AtcParams {
   int32_t* iters_out;
   uint8_t* conv_out;
   int* status;
+  unsigned long long* counter;  // next pixel to hand out (zeroed before the launch)
   int inject_timeout;  // test hook: the first product is not issued (see launch_admm_tc)
 };
 
@@ -64,7 +65,8 @@ struct Shape {
   static_assert(2 * NP <= 512 && MP <= NP, "TMEM columns");
   static_assert(NP % 16 == 0 && MP % 16 == 0, "MMA shapes");
   static_assert(QM <= 2 && QM <= NBUF, "chunk plan");
-  static_assert(A_BYTES + W_BYTES + 2 * kBufBytes + 2048 <= 227 * 1024, "shared memory");
+  // dynamic plus about 1 KB of static shared memory (barriers, lane pixels)
+  static_assert(A_BYTES + W_BYTES + 2 * kBufBytes + 1024 + 1024 <= 227 * 1024, "shared memory");
   // chunk q of an L-column operand: start, width
   __host__ __device__ static constexpr int cw(int L, int q) {
     return L - kChunk * q < kChunk ? L - kChunk * q : kChunk;
@@ -75,6 +77,22 @@ struct Shape {
 
 using tc::put_operand8;
 using tc::soft_thr;
+
+// The finished lanes of a warp (fin) take the next pixels from the counter with one
+// atomic: lane by lane in order, -1 once none is left.  All 32 lanes call it.
+__device__ __forceinline__ void claim_pixels(bool fin, unsigned long long* counter, int64_t P,
+                                             int* s_pix, int r, int lane) {
+  const unsigned m = __ballot_sync(0xffffffffu, fin);
+  if (!m) return;
+  const int leader = __ffs(m) - 1;
+  unsigned long long base = 0;
+  if (lane == leader) base = atomicAdd(counter, (unsigned long long)__popc(m));
+  base = __shfl_sync(0xffffffffu, base, leader);
+  if (fin) {
+    const unsigned long long nx = base + __popc(m & ((1u << lane) - 1u));
+    s_pix[r] = nx < (unsigned long long)P ? (int)nx : -1;
+  }
+}
 
 // The split MMAs (hi*hi, lo*hi, hi*lo) of `steps` K-steps of 16: the operand at a (hi; lo
 // at a + kLoOff, K-major in a 64-column buffer) against the matrix at bh / bl.
@@ -101,6 +119,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_admm_tc(AtcParams p) {
   __shared__ __align__(8) uint64_t mb_drain;   // every MMA issued so far completed
   __shared__ uint32_t tmem_slot;
   __shared__ int s_fail;
+  __shared__ int s_pix[128];  // the pixel each TMEM lane holds (-1: none left; P < 2^31)
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int sub = warp & 3, g = warp >> 2;
   const int r = 32 * sub + lane;  // tile row == TMEM lane
@@ -113,8 +132,6 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_admm_tc(AtcParams p) {
   unsigned char* sB = sWl + MP * MP * 2;  // operand ring
   float* red = reinterpret_cast<float*>(sB + S::NBUF * kBufBytes);  // [2][128]
 
-  const int64_t pix = (int64_t)blockIdx.x * 128 + r;
-  const bool valid = pix < p.P;
 
   // A (M x N) and W (M x M) split into BF16 hi + lo in the dual layout: GEMM1 reads A
   // K-major (A^T), GEMM2 reads A and GEMMW reads W MN-major
@@ -125,6 +142,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_admm_tc(AtcParams p) {
     tc::mbar_init(&mb_done, 1);
     tc::mbar_init(&mb_drain, 1);
     s_fail = 0;
+    s_pix[0] = (int)min(atomicAdd(p.counter, 128ull), (unsigned long long)p.P);  // this CTA's first 128 pixels
   }
   if (warp == 0) tc::tmem_alloc(&tmem_slot, S::TCOLS);
   tc::fence_async_smem();
@@ -138,11 +156,18 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_admm_tc(AtcParams p) {
   const uint32_t tV = tl + NP;  // the iterate v, columns [NP, 2 NP)
   const uint32_t uB = tc::smem_u32(sB), uAh = tc::smem_u32(sAh), uAl = tc::smem_u32(sAl);
   const uint32_t uWh = tc::smem_u32(sWh), uWl = tc::smem_u32(sWl);
+  // the grid is persistent: every TMEM lane holds one pixel and takes the next one from
+  // the counter when its pixel finishes, so converged pixels leave no idle lanes behind
+  int64_t pix = (int64_t)s_pix[0] + r;
+  __syncthreads();
+  if (pix >= p.P) pix = -1;
+  bool valid = pix >= 0;
 
   float yv[S::MH], hp[S::MH];
-  bool bad = false;
-  {
+  // y and h^0 = y / rho (r^0 = y) of the pixel this lane holds
+  auto load_y = [&]() {
     const float* yrow = p.Y + (valid ? pix : 0) * M;
+    bool bad = false;
 #pragma unroll
     for (int k = 0; k < S::QM; ++k) {
       const int c0 = kChunk * k + g * (S::cw(MP, k) / 2);
@@ -152,10 +177,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_admm_tc(AtcParams p) {
         const float v = (valid && m < M) ? __ldg(yrow + m) : 0.f;
         bad |= !isfinite(v);
         yv[S::ro(k) + c] = v;
-        hp[S::ro(k) + c] = v / p.rho;  // r^0 = y = rho h^0
+        hp[S::ro(k) + c] = v / p.rho;
       }
     }
     if (bad) atomicOr(p.status, kStNonFinite);
+  };
+  {
+    load_y();
     const float zero8[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
 #pragma unroll
     for (int q = 0; q < S::QN; ++q)
@@ -165,15 +193,27 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_admm_tc(AtcParams p) {
     tc::tmem_wait_st();
   }
   bool done = !valid;
-  if (valid && (p.start_done || p.iters == 0)) {
-    // no iteration: x = x^0 = 0
-    for (int n = g; n < N; n += 2) p.X[pix * N + n] = 0.f;
-    if (g == 0) {
-      if (p.iters_out) p.iters_out[pix] = 0;
-      if (p.conv_out) p.conv_out[pix] = 0;
+  if (p.start_done || p.iters == 0) {
+    // no iteration: x = x^0 = 0 for every pixel, each lane taking pixels until none is
+    // left (the barriers are reached by every thread: the loop test is block-wide)
+    while (__syncthreads_or(valid)) {
+      if (valid) {
+        for (int n = g; n < N; n += 2) p.X[pix * N + n] = 0.f;
+        if (g == 0) {
+          if (p.iters_out) p.iters_out[pix] = 0;
+          if (p.conv_out) p.conv_out[pix] = 0;
+        }
+      }
+      if (g == 0) claim_pixels(valid, p.counter, p.P, s_pix, r, lane);
+      __syncthreads();
+      if (valid) {
+        pix = s_pix[r];
+        valid = pix >= 0;
+      }
     }
     done = true;
   }
+  int k_it = 1;  // the lane's own iteration number
 
   const uint32_t id1 = tc::idesc_bf16(128, MP, false);  // T = D A^T
   const uint32_t idw = tc::idesc_bf16(128, MP, true);   // H = E W
@@ -317,7 +357,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_admm_tc(AtcParams p) {
       pending |= (1u << S::QM) - 1u;
       const float dtot = p.rho * p.rho * (red[r] + red[128 + r]);
       const bool conv_now = !done && dtot < p.eps2;
-      const bool fin = !done && (conv_now || i == p.iters);
+      const bool fin = !done && (conv_now || k_it == p.iters);
       wait_done();
       // ---- x = d + C, z = soft(v, lambda / rho), w = v - z; the next v = z + C
 #pragma unroll
@@ -351,18 +391,47 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_admm_tc(AtcParams p) {
         }
       }
       tc::tmem_wait_st();
+      // a finished lane's next pixel starts from v = 0 (out of the hot loop above; the
+      // TMEM stores are warp-wide, so the warp's other lanes write their v back)
+      if (__any_sync(0xffffffffu, fin)) {
+#pragma unroll
+        for (int q = 0; q < S::QN; ++q) {
+          const int c0 = kChunk * q + g * (S::cw(NP, q) / 2);
+#pragma unroll
+          for (int c = 0; c < S::cw(NP, q) / 2; c += 8) {
+            float vv[8];
+            tc::tmem_ld8(tV + c0 + c, vv);
+            tc::tmem_wait_ld();
+#pragma unroll
+            for (int e = 0; e < 8; ++e) vv[e] = fin ? 0.f : vv[e];
+            tc::tmem_st8(tV + c0 + c, vv);
+          }
+        }
+        tc::tmem_wait_st();
+      }
       if (fin && g == 0) {
-        if (p.iters_out) p.iters_out[pix] = i;
+        if (p.iters_out) p.iters_out[pix] = k_it;
         if (p.conv_out) p.conv_out[pix] = conv_now ? 1 : 0;
       }
+      // a finished lane takes the next pixel: its group-0 thread claims it for the row,
+      // one atomic per warp for all of the warp's finished lanes
+      if (g == 0) claim_pixels(fin, p.counter, p.P, s_pix, r, lane);
       done = done || fin;
       if (failed) s_fail = 1;
       tc::fence_before_sync();
-      if (!__syncthreads_or(!done)) break;
+      if (!__syncthreads_or(!done || (fin && g == 0 && s_pix[r] >= 0))) break;
       tc::fence_after_sync();
       if (s_fail) {
         failed = true;
         break;
+      }
+      ++k_it;
+      if (fin) {
+        pix = s_pix[r];
+        valid = pix >= 0;
+        done = !valid;
+        k_it = 1;
+        if (valid) load_y();
       }
     }
   }
@@ -391,8 +460,11 @@ cudaError_t run(const Ctx& c, const AtcParams& p) {
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
-  unsigned grid = (unsigned)((p.P + 127) / 128);
-  kern<<<grid, kTcThreads, smem, c.stream>>>(p);
+  long long grid = (p.P + 127) / 128;
+  if (grid > c.num_sms) grid = c.num_sms;  // persistent: one CTA (all of TMEM) per SM
+  e = cudaMemsetAsync(p.counter, 0, sizeof(unsigned long long), c.stream);
+  if (e != cudaSuccess) return e;
+  kern<<<(unsigned)grid, kTcThreads, smem, c.stream>>>(p);
   return cudaGetLastError();
 }
 
@@ -427,6 +499,7 @@ cudaError_t launch_admm_tc(const Ctx& c, const ConvexArgs& a) {
   p.iters_out = a.iters_out;
   p.conv_out = a.conv_out;
   p.status = c.status;
+  p.counter = a.counter ? a.counter : c.conv_counter;
   p.inject_timeout = tc::inject_timeout();
   if (a.P == 0) return cudaSuccess;
   const int Mp = (c.M + 15) / 16 * 16, Np = (c.N + 15) / 16 * 16;

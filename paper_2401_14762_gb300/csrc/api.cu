@@ -61,6 +61,7 @@ void free_ctx(Ctx& c) {
   cudaFree(c.stage_aux);
   cudaFree(c.fb64);
   cudaFree(c.work);
+  cudaFree(c.conv_counter);
   cudaFree(c.beta);
   for (int k = 0; k < Ctx::kAux; ++k) {
     if (c.aux[k]) cudaStreamDestroy(c.aux[k]);
@@ -100,6 +101,21 @@ cudaError_t ensure_pipe(Ctx& c, int64_t pixels) {
   if (e == cudaSuccess) c.pipe_cap = pixels;
   return e;
 }
+
+}  // namespace
+
+cudaError_t ensure_conv_counters(Ctx& c, int n) {
+  if (c.conv_counter_cap >= n) return cudaSuccess;
+  cudaFree(c.conv_counter);
+  c.conv_counter = nullptr;
+  c.conv_counter_cap = 0;
+  cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&c.conv_counter),
+                             sizeof(unsigned long long) * (size_t)n);
+  if (e == cudaSuccess) c.conv_counter_cap = n;
+  return e;
+}
+
+namespace {
 
 // The fork-join streams and events of multi-cube convex batches, created once.
 cudaError_t ensure_aux(Ctx& c) {
@@ -248,6 +264,7 @@ cs_status cs_create(cs_ctx** out, int M, int N, const double* A_host, const doub
       (e = cs::dalloc(&c.status, 1)) != cudaSuccess ||
       (e = cs::dalloc(&c.counter, 2)) != cudaSuccess ||
       (e = cs::dalloc(&c.work, 1)) != cudaSuccess ||
+      (e = cs::ensure_conv_counters(c, 2)) != cudaSuccess ||
       (!A_host && ((e = cs::dalloc(&c.Psi64, (size_t)N * N)) != cudaSuccess ||
                    (e = cs::dalloc(&c.Psi32, (size_t)N * 128 * ((N + 127) / 128))) !=
                        cudaSuccess ||
@@ -544,6 +561,10 @@ cs_status cs_recover_batch(const cs_batch_item* items, int n_items, cs_algo algo
     c.stream = own_stream;
     if (e != cudaSuccess) return cuda_fail(e, "batched convex setup");
   }
+  // each launch counts its pixels in its own slot of c0's counters (the launches of
+  // several cubes, even of one context, may run at the same time)
+  e = cs::ensure_conv_counters(c0, (int)order.size() + 2);
+  if (e != cudaSuccess) return cuda_fail(e, "batch counters");
   const bool fork = order.size() > 1;
   int used = 0;
   if (fork) {
@@ -563,7 +584,7 @@ cs_status cs_recover_batch(const cs_batch_item* items, int n_items, cs_algo algo
     c.stream = fork ? c0.aux[j % cs::Ctx::kAux] : c0.stream;
     c.status = c0.status;
     cs::ConvexArgs a{it.Y, it.X, it.P, params->lambda, params->rho, o.eps, params->iters,
-                     it.iters_out, it.converged_out, o.prec};
+                     it.iters_out, it.converged_out, o.prec, c0.conv_counter + 2 + j};
     e = algo == CS_ALGO_ADMM ? cs::launch_admm(c, a) : cs::launch_fista(c, a, false);
     c.stream = own_stream;
     c.status = own_status;
@@ -650,7 +671,7 @@ cs_status cs_recover_stream(cs_ctx* ctx, cs_algo algo, const cs_algo_params* par
       e = cs::launch_greedy(c, ga, a);
     } else {
       cs::ConvexArgs a{c.pipe_y[b], c.pipe_x[b], n, params->lambda, params->rho, o.eps,
-                       params->iters, it, cv, o.prec};
+                       params->iters, it, cv, o.prec, c.conv_counter + b};
       e = algo == CS_ALGO_ADMM ? cs::launch_admm(c, a) : cs::launch_fista(c, a, false);
     }
     c.stream = own;

@@ -66,6 +66,11 @@ struct Ctx {
   size_t scratch_elems = 0;
   int* status = nullptr;      // device status word
   int* counter = nullptr;     // work counter of the persistent greedy kernel
+  // pixel counters of the persistent tensor-core FISTA/ADMM launches: slot 0 for single
+  // calls, one per chunk buffer of streamed calls and one per cube of convex batches
+  // (launches that may run at the same time need their own)
+  unsigned long long* conv_counter = nullptr;
+  int conv_counter_cap = 0;
   double* fb64 = nullptr;     // per-warp FP64 fallback slots of the greedy kernel
   double* work = nullptr;     // algorithmic flops of the last greedy call (device, 1 entry)
   float* beta = nullptr;      // FISTA momentum weights (device), capacity beta_cap
@@ -117,6 +122,7 @@ struct ConvexArgs {
   int32_t* iters_out;
   uint8_t* conv_out;
   cs_precision prec;
+  unsigned long long* counter = nullptr;  // tensor-core pixel counter (null: the context's slot 0)
 };
 // FISTA's momentum weights beta_i (i = 1..iters) into c.beta, on c.stream
 cudaError_t momentum_table(Ctx& c, int iters);
@@ -125,6 +131,8 @@ cudaError_t launch_fista(Ctx& c, const ConvexArgs& a, bool table = true);
 bool fista_tc_supported(int M, int N);
 cudaError_t launch_fista_tc(const Ctx& c, const ConvexArgs& a);
 cudaError_t launch_admm(Ctx& c, const ConvexArgs& a);
+// at least n pixel-counter slots in c.conv_counter
+cudaError_t ensure_conv_counters(Ctx& c, int n);
 bool admm_tc_supported(int M, int N);
 cudaError_t launch_admm_tc(const Ctx& c, const ConvexArgs& a);
 

@@ -55,6 +55,7 @@ struct FtcParams {
   uint8_t* conv_out;
   int* status;
   const float* beta;   // momentum weights beta_i, i = 1..iters
+  unsigned long long* counter;  // next pixel to hand out (zeroed before the launch)
   int inject_timeout;  // test hook: the first product is not issued (see launch_fista_tc)
 };
 
@@ -114,6 +115,22 @@ struct Shape {
 using tc::put_operand8;
 using tc::soft_thr;
 
+// The finished lanes of a warp (fin) take the next pixels from the counter with one
+// atomic: lane by lane in order, -1 once none is left.  All 32 lanes call it.
+__device__ __forceinline__ void claim_pixels(bool fin, unsigned long long* counter, int64_t P,
+                                             int* s_pix, int r, int lane) {
+  const unsigned m = __ballot_sync(0xffffffffu, fin);
+  if (!m) return;
+  const int leader = __ffs(m) - 1;
+  unsigned long long base = 0;
+  if (lane == leader) base = atomicAdd(counter, (unsigned long long)__popc(m));
+  base = __shfl_sync(0xffffffffu, base, leader);
+  if (fin) {
+    const unsigned long long nx = base + __popc(m & ((1u << lane) - 1u));
+    s_pix[r] = nx < (unsigned long long)P ? (int)nx : -1;
+  }
+}
+
 // Issues the split MMAs (hi*hi, lo*hi, hi*lo) of `steps` K-steps of 16: the operand at
 // a (hi; lo at a + kLoOff, K-major, 64 K-columns per buffer row group) against the
 // dictionary at bh / bl.
@@ -139,6 +156,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_fista_tc(FtcParams p) {
                                            // and the drain after a failed wait
   __shared__ uint32_t tmem_slot;
   __shared__ int s_fail;  // a bounded wait ran out (set by any thread, read after a barrier)
+  __shared__ int s_pix[128];  // the pixel each TMEM lane holds (-1: none left; P < 2^31)
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int sub = warp & 3, g = warp >> 2;
   const int r = 32 * sub + lane;  // tile row == TMEM lane
@@ -149,8 +167,6 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_fista_tc(FtcParams p) {
   unsigned char* sB = sAl + MP * NP * 2;  // operand ring
   float* red = reinterpret_cast<float*>(sB + S::NBUF * kBufBytes);  // [2][128]
 
-  const int64_t pix = (int64_t)blockIdx.x * 128 + r;
-  const bool valid = pix < p.P;
 
   // A (M x N) split into BF16 hi + lo (from FP64) in the dual layout, zero padded to
   // MP x NP: GEMM1 reads it K-major (A^T), GEMM2 MN-major
@@ -158,6 +174,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_fista_tc(FtcParams p) {
   if (tid == 0) {
     for (int k = 0; k < 5; ++k) tc::mbar_init(&mb[k], 1);
     s_fail = 0;
+    s_pix[0] = (int)min(atomicAdd(p.counter, 128ull), (unsigned long long)p.P);  // this CTA's first 128 pixels
   }
   if (warp == 0) tc::tmem_alloc(&tmem_slot, S::TCOLS);
   tc::fence_async_smem();
@@ -168,6 +185,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_fista_tc(FtcParams p) {
   const uint32_t tmem = tmem_slot;
   const uint32_t tl = tmem + ((uint32_t)(32 * sub) << 16);
   const uint32_t tX = tl + 2 * S::RW;  // iterate x, columns [2 RW, 2 RW + NP)
+  // the grid is persistent: every TMEM lane holds one pixel and takes the next one from
+  // the counter when its pixel finishes, so converged pixels leave no idle lanes behind
+  int64_t pix = (int64_t)s_pix[0] + r;
+  __syncthreads();
+  if (pix >= p.P) pix = -1;
+  bool valid = pix >= 0;
   const uint32_t uB = tc::smem_u32(sB), uAh = tc::smem_u32(sAh), uAl = tc::smem_u32(sAl);
 
   // z in registers; R = u - y = A x - y, the residual of the iterate, in registers too:
@@ -176,11 +199,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_fista_tc(FtcParams p) {
   // need.  The split product of an increment errs relative to the increment, so y is
   // read once and the residual never loses accuracy to the size of A x.
   float z[S::NH], R[S::MH];
-  bool bad = false;
 #pragma unroll
   for (int j = 0; j < S::NH; ++j) z[j] = 0.f;
-  {
+  // R = -y of the pixel this lane holds (u^0 = 0)
+  auto load_residual = [&]() {
     const float* yrow = p.Y + (valid ? pix : 0) * M;
+    bool bad = false;
 #pragma unroll
     for (int k = 0; k < S::KW; ++k) {
       const int c0 = S::wc(k) + g * (S::ww(k) / 2);
@@ -189,10 +213,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_fista_tc(FtcParams p) {
         const int m = c0 + c;
         const float yv = (valid && m < M) ? __ldg(yrow + m) : 0.f;
         bad |= !isfinite(yv);
-        R[S::uo(k) + c] = -yv;  // u^0 = 0
+        R[S::uo(k) + c] = -yv;
       }
     }
     if (bad) atomicOr(p.status, kStNonFinite);
+  };
+  {
+    load_residual();
     const float zero8[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
 #pragma unroll
     for (int q = 0; q < S::Q; ++q)
@@ -203,6 +230,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_fista_tc(FtcParams p) {
   }
 
   bool done = !valid;
+  int k_it = 1;          // the lane's own iteration number (its pixel's x^{k_it - 1} is in TMEM)
   float beta_prev = 0.f;
   uint32_t ph = 0;   // phase parity of the four mbarriers in this iteration
   int ui = 0;        // region holding D (T0 = columns [0, RW), T1 = [RW, 2 RW))
@@ -251,9 +279,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_fista_tc(FtcParams p) {
     __syncthreads();
     failed = s_fail != 0;
     const float dtot = red[r] + red[128 + r];
-    // x^{i-1} is final if Delta_{i-1} < eps, if the cap is reached, or (eps > 1) at once
-    const bool conv_now = !done && i > 1 && dtot < p.eps2;
-    const bool fin = !done && (conv_now || i - 1 == p.iters || (i == 1 && p.start_done));
+    // x^{k-1} is final if Delta_{k-1} < eps, if the cap is reached, or (eps > 1) at once
+    const bool conv_now = !done && k_it > 1 && dtot < p.eps2;
+    const bool fin =
+        !done && (conv_now || k_it - 1 == p.iters || (k_it == 1 && p.start_done));
     if (__any_sync(0xffffffffu, fin)) {
 #pragma unroll
       for (int q = 0; q < S::Q; ++q) {
@@ -271,16 +300,28 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_fista_tc(FtcParams p) {
         }
       }
       if (fin && g == 0) {
-        if (p.iters_out) p.iters_out[pix] = i - 1;
+        if (p.iters_out) p.iters_out[pix] = k_it - 1;
         if (p.conv_out) p.conv_out[pix] = conv_now ? 1 : 0;
       }
     }
+    // a finished lane takes the next pixel: its group-0 thread claims it for the row, one
+    // atomic per warp for all of the warp's finished lanes
+    if (g == 0) claim_pixels(fin, p.counter, p.P, s_pix, r, lane);
     done = done || fin;
     tc::fence_async_smem();
     tc::fence_before_sync();
     // a product that never completed ends the solve for the whole tile
-    if (!__syncthreads_or(!done) || failed) break;
+    if (!__syncthreads_or(!done || (fin && g == 0 && s_pix[r] >= 0)) || failed) break;
     tc::fence_after_sync();
+    // fresh: the lane starts a new pixel; this iteration's products for it are discarded
+    // (its increment is 0, so the next D is 0 too, and x and z are then set to 0)
+    bool fresh = false;
+    if (fin) {
+      pix = s_pix[r];
+      valid = pix >= 0;
+      fresh = valid;
+      done = !valid;
+    }
 
     // ---- GEMM2: C = V A in two column halves, half 0 into the free region, half 1 into
     //      the region D was read from (K = MP over the residual's chunks)
@@ -302,7 +343,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_fista_tc(FtcParams p) {
 
     // ---- steps 1-4 chunk by chunk: aux = z - C / L, x = soft(aux, lambda / L), t, z;
     //      x to TMEM and its increment x - x_prev, split, to the ring for GEMM1
-    const float beta = p.beta[i - 1];
+    const float beta = p.beta[min(k_it, p.iters > 0 ? p.iters : 1) - 1];
+    const bool hold = done || fresh;
 #pragma unroll
     for (int q = 0; q < S::Q; ++q) {
       if (q == 0) failed |= !tc::mbar_wait(&mb[0], ph, kWaitLimitNs);
@@ -333,7 +375,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_fista_tc(FtcParams p) {
             for (int e = 0; e < 8; ++e) {
               const int j = S::zo(q) + c + e;
               float xx = soft_thr(z[j] - C[h][e] * p.invL, p.thr);
-              if (!done) {
+              if (!hold) {
                 z[j] = xx + beta * (xx - xp[h][e]);
               } else {
                 xx = xp[h][e];
@@ -371,11 +413,39 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_fista_tc(FtcParams p) {
         }
       }
     }
+    // a lane starting a new pixel: x = 0 in TMEM and z = 0 (out of the hot loop above;
+    // the TMEM stores are warp-wide, so the warp's other lanes write their x back)
+    if (__any_sync(0xffffffffu, fresh)) {
+#pragma unroll
+      for (int q = 0; q < S::Q; ++q) {
+        const int c0 = S::xc(q) + g * (S::xw(q) / 2);
+#pragma unroll
+        for (int c = 0; c < S::xw(q) / 2; c += 8) {
+          float xv[8];
+          tc::tmem_ld8(tX + c0 + c, xv);
+          tc::tmem_wait_ld();
+#pragma unroll
+          for (int e = 0; e < 8; ++e) xv[e] = fresh ? 0.f : xv[e];
+          tc::tmem_st8(tX + c0 + c, xv);
+        }
+      }
+      tc::tmem_wait_st();
+      if (fresh) {
+#pragma unroll
+        for (int j = 0; j < S::NH; ++j) z[j] = 0.f;
+      }
+    }
     failed |= !tc::mbar_wait(&mb[3], ph, kWaitLimitNs);
     tc::fence_after_sync();
     ph ^= 1u;
     ui = 1 - ui;
     beta_prev = beta;
+    ++k_it;
+    if (fresh) {  // the new pixel's first iteration comes next
+      load_residual();
+      k_it = 1;
+      beta_prev = 0.f;
+    }
   }
   if (__syncthreads_or(failed)) {
     // a product never completed: report, then one commit that tracks every MMA thread 0
@@ -401,8 +471,11 @@ cudaError_t run(const Ctx& c, const FtcParams& p) {
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
-  unsigned grid = (unsigned)((p.P + 127) / 128);
-  kern<<<grid, kTcThreads, smem, c.stream>>>(p);
+  long long grid = (p.P + 127) / 128;
+  if (grid > c.num_sms) grid = c.num_sms;  // persistent: one CTA (all of TMEM) per SM
+  e = cudaMemsetAsync(p.counter, 0, sizeof(unsigned long long), c.stream);
+  if (e != cudaSuccess) return e;
+  kern<<<(unsigned)grid, kTcThreads, smem, c.stream>>>(p);
   return cudaGetLastError();
 }
 
@@ -437,6 +510,7 @@ cudaError_t launch_fista_tc(const Ctx& c, const ConvexArgs& a) {
   p.conv_out = a.conv_out;
   p.status = c.status;
   p.beta = c.beta;
+  p.counter = a.counter ? a.counter : c.conv_counter;
   p.inject_timeout = tc::inject_timeout();
   if (a.P == 0) return cudaSuccess;
   const int Mp = (c.M + 15) / 16 * 16, Np = (c.N + 15) / 16 * 16;
