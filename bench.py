@@ -850,7 +850,15 @@ def run_only(args):
         "gomp": lambda: cs.cs_recover_gomp(ctx, Y, X, KAPPA, G, cs.make_opts(eps=EPS)),
         "biht": lambda: cs.cs_recover_biht(ctx, Y, X, KAPPA, cs.make_opts(eps=EPS, mu=MU)),
         "cosamp": lambda: cs.cs_recover_cosamp(ctx, Y, X, KAPPA, cs.make_opts(eps=EPS)),
+        # the sparsification pre-processing on spectra f = Psi x (X holds f here)
+        "sparsify": lambda: cs.cs_sparsify(ctx, X, Y2, 0.1, 1),
     }
+    if args.only == "sparsify":
+        g = torch.Generator(device=dev)
+        g.manual_seed(SEED)
+        X.copy_((Xt.double() @ dct_psi(N, dev).T + 0.01 * torch.randn(
+            (n, N), generator=g, device=dev, dtype=torch.float64)).float())
+        Y2 = torch.empty((n, N), device=dev)
     for _ in range(2):
         calls[args.only]()
     cs.cs_sync(ctx)
@@ -867,7 +875,7 @@ def main():
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--only", default=None,
                     choices=["measure", "fista", "fista_fp32", "admm", "gomp", "biht",
-                             "cosamp"])
+                             "cosamp", "sparsify"])
     ap.add_argument("--pixels", type=int, default=16384)
     ap.add_argument("--no-batch", action="store_true",
                     help="skip the 64-cube batching measurement")

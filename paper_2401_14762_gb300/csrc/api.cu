@@ -63,6 +63,7 @@ void free_ctx(Ctx& c) {
   cudaFree(c.work);
   cudaFree(c.conv_counter);
   cudaFree(c.beta);
+  for (float* b : c.beta_retired) cudaFree(b);
   for (int k = 0; k < Ctx::kAux; ++k) {
     if (c.aux[k]) cudaStreamDestroy(c.aux[k]);
     if (c.ev_join[k]) cudaEventDestroy(c.ev_join[k]);

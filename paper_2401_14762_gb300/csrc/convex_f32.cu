@@ -553,17 +553,24 @@ cudaError_t admm_mr(const Ctx& c, CvParams p, int64_t blocks) {
   } while (0)
 
 cudaError_t momentum_table(Ctx& c, int iters) {
+  // beta_i does not depend on the run length, so a context computes the sequence once
+  // for the longest run it has seen and later calls read its prefix
+  if (iters <= c.beta_valid) return cudaSuccess;
   if (c.beta_cap < iters || !c.beta) {
-    cudaFree(c.beta);
-    c.beta = nullptr;
-    c.beta_cap = 0;
-    int cap = iters > 1024 ? iters : 1024;
-    cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&c.beta), sizeof(float) * cap);
+    int cap = iters > 2 * c.beta_cap ? iters : 2 * c.beta_cap;
+    if (cap < 1024) cap = 1024;
+    float* nb = nullptr;
+    cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&nb), sizeof(float) * cap);
     if (e != cudaSuccess) return e;
+    if (c.beta) c.beta_retired.push_back(c.beta);
+    c.beta = nb;
     c.beta_cap = cap;
+    c.beta_valid = 0;
   }
-  k_momentum<<<1, 1, 0, c.stream>>>(iters, c.beta);
-  return cudaGetLastError();
+  k_momentum<<<1, 1, 0, c.stream>>>(c.beta_cap, c.beta);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) c.beta_valid = c.beta_cap;
+  return e;
 }
 
 cudaError_t launch_fista(Ctx& c, const ConvexArgs& a, bool table) {

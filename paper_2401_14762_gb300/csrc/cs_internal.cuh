@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 #include "cs_hsi.h"
 
@@ -75,6 +76,10 @@ struct Ctx {
   double* work = nullptr;     // algorithmic flops of the last greedy call (device, 1 entry)
   float* beta = nullptr;      // FISTA momentum weights (device), capacity beta_cap
   int beta_cap = 0;
+  int beta_valid = 0;         // leading entries of beta already computed
+  // tables outgrown by a longer call: kept until the context is destroyed, so that a
+  // graph captured while one of them was current still reads valid memory
+  std::vector<float*> beta_retired;
   void* cube_table = nullptr; // greedy launches' cube descriptors (device), cube_cap entries
   int cube_cap = 0;
   size_t fb64_elems = 0;
@@ -124,7 +129,8 @@ struct ConvexArgs {
   cs_precision prec;
   unsigned long long* counter = nullptr;  // tensor-core pixel counter (null: the context's slot 0)
 };
-// FISTA's momentum weights beta_i (i = 1..iters) into c.beta, on c.stream
+// FISTA's momentum weights beta_i (i = 1..iters) into c.beta, on c.stream (only the
+// first time a context needs that many: the table of a shorter run is a prefix)
 cudaError_t momentum_table(Ctx& c, int iters);
 // table = false: c.beta already holds at least a.iters weights (batches write it once)
 cudaError_t launch_fista(Ctx& c, const ConvexArgs& a, bool table = true);

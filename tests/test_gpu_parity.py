@@ -106,6 +106,20 @@ def test_fista_small_long_run_meets_fp32_bar(cs, small):
     assert rel_l2(Xg, Xo) <= REL_L2_FP32
 
 
+def test_fista_momentum_table_reused_across_run_lengths(cs, small):
+    """A context computes the momentum sequence once for its longest run: a short run, a
+    longer run that outgrows the table, and the short run again give the bits that fresh
+    contexts give for the same lengths."""
+    def run(ctx, iters):
+        return gpu_run(cs.cs_recover_fista, ctx, small.Y, small.N, 1e-3, iters, eps=0.0)[0]
+    ctx = cs.cs_create(small.M, small.N, Phi=small.Phi)
+    short1, long1, short2 = run(ctx, 40), run(ctx, 2500), run(ctx, 40)
+    fresh_short = run(cs.cs_create(small.M, small.N, Phi=small.Phi), 40)
+    fresh_long = run(cs.cs_create(small.M, small.N, Phi=small.Phi), 2500)
+    assert np.array_equal(short1, fresh_short) and np.array_equal(short2, fresh_short)
+    assert np.array_equal(long1, fresh_long)
+
+
 def test_fista_powerlaw(cs, plaw):
     _fista_fixed(cs, plaw, 1e-3, 300)
 
