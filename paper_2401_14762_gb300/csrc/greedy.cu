@@ -90,8 +90,8 @@ struct GrParams {
 // sized for FP64 (the fallback factorisation then runs in place); otherwise they hold
 // the FP32 factors only and the fallback uses the warp's global slot.
 struct Layout {
-  int y, rf, xd, b32, bx, bk, inc, c, q, qp, sel, xq, xqp, xqf, L, invd, v, s, wv, Lq, invq,
-      vq, sq, svals, cx, cq, ring, total;
+  int y, y64, rf, xd, b32, bx, bk, inc, c, q, qp, qf, sel, xq, xqp, xqf, L, invd, v, s, wv, Lq,
+      invq, vq, sq, svals, cx, cq, ring, total;
   __host__ __device__ Layout(int M, int N, int cmax, int dmax, int kmax, int selmax,
                              bool fp64_smem, bool need_q, bool need_cyc, bool need_xd,
                              int d32) {
@@ -104,20 +104,23 @@ struct Layout {
       return at;
     };
     bx = take(8 * N, 8);  // A^T y in FP64, filled in for support atoms
+    y64 = take(8 * M, 8);  // y in FP64 (exact), for the FP64 products with y
     xq = take(8 * kmax, 8);
     xqp = take(8 * kmax, 8);  // the previous iterate's kept coefficients (Delta)
     const int df = fp64_smem ? dmax : d32;  // factor rows held here
     L = take(fw * (df * (df + 1) / 2), 8);
     invd = take(fw * df, 8);
-    v = take(8 * dmax, 8);
+    // the in-place FP64 fallback's vectors (else they live in the warp's global slot)
+    v = take(fp64_smem ? 8 * dmax : 0, 8);
     s = take(8 * cmax, 8);
-    wv = take(8 * dmax, 8);
+    wv = take(fp64_smem ? 8 * dmax : 0, 8);
     const int kq = need_q ? kmax : 0;
     Lq = take(fw * (kq * (kq + 1) / 2), 8);
     invq = take(fw * kq, 8);
-    vq = take(8 * kq, 8);
+    vq = take(fp64_smem ? 8 * kq : 0, 8);
     sq = take(8 * kq, 8);
-    svals = take(8 * cmax, 8);
+    // the minimum-norm solve's H^{-1} y (BIHT and CoSaMP; gOMP's support never exceeds M)
+    svals = take(need_q ? 0 : 8 * cmax, 8);
     const int kc = need_cyc ? kmax : 0;  // saved iterate of the cycle search
     cx = take(8 * kc, 8);
     ring = take(need_cyc ? 8 * 32 : 0, 8);  // hashes of the last 32 iterates
@@ -129,6 +132,7 @@ struct Layout {
     c = take(2 * cmax, 2);
     q = take(2 * kmax, 2);
     qp = take(2 * kmax, 2);
+    qf = take(2 * kq, 2);  // atoms of the rows the refit factor Lq holds (gOMP)
     cq = take(2 * kc, 2);
     sel = take(2 * selmax, 2);  // a selection: G, 2 kappa or kappa atoms, or kappa positions
     inc = take(N, 1);
@@ -146,14 +150,11 @@ struct Warp {
   int lane;
   const GrCube* cb;  // the cube of the pixel in hand (device table entry)
   float *y, *rf, *xd, *b32, *xqf;
-  double *bx, *xq, *xqp, *L, *invd, *v, *s, *wv, *Lq, *invq, *vq, *sq, *svals;
+  double *y64, *bx, *xq, *xqp, *L, *invd, *v, *s, *wv, *Lq, *invq, *vq, *sq, *svals;
   uint8_t *inc, *bk;
-  int16_t *c, *q, *qp, *sel;
+  int16_t *c, *q, *qp, *qf, *sel;
   double* fb;  // this warp's global FP64 fallback slot, or nullptr
 };
-
-// (A^T y)_j in FP64 (computed by ensure_rhs before any use).
-__device__ __forceinline__ double rhs(Warp& w, int j) { return w.bx[j]; }
 
 // b32 = A^T y in FP32 for every atom (the correlation's first term): lanes own atoms,
 // rows of A are read coalesced, each sum in the order m = 0, 1, ...
@@ -181,19 +182,51 @@ __device__ void load_rhs32(Warp& w) {
 
 // (A^T y)_j in FP64 for every atom of atoms[0..n) not yet known: the M products of
 // column j of A with y, lanes over the rows (contiguous in A^T), summed across the warp.
+// Up to four atoms share one reduction: a first exchange (lanes 16 apart) trades two of
+// the four partial sums, a second (8 apart) one of the remaining two, and three more
+// finish the sum, which leaves atom i's total on lanes 8i..8i+7 after six FP64 additions
+// instead of twenty.  Every total is added in the order a single-value butterfly over
+// lanes 16, 8, 4, 2, 1 apart uses.
 __device__ void ensure_rhs(Warp& w, const int16_t* atoms, int n) {
-  const int M = w.cb->M;
-  for (int t = 0; t < n; ++t) {
-    const int j = atoms[t];
-    if (w.bk[j]) continue;  // warp-uniform (shared-memory broadcast)
-    const double* a = w.cb->At64 + (size_t)j * M;
-    double acc = 0.0;
-    for (int m = w.lane; m < M; m += 32) acc = fma(__ldg(a + m), (double)w.y[m], acc);
-    acc = warp_sum(acc);
+  const int M = w.cb->M, lane = w.lane;
+  const double* At = w.cb->At64;
+  int t = 0;
+  for (;;) {
+    int j0 = -1, j1 = -1, j2 = -1, j3 = -1;  // warp-uniform (shared-memory broadcasts)
+    for (; t < n && j3 < 0; ++t) {
+      const int j = atoms[t];
+      if (w.bk[j]) continue;
+      if (j0 < 0) j0 = j;
+      else if (j1 < 0) j1 = j;
+      else if (j2 < 0) j2 = j;
+      else j3 = j;
+    }
+    if (j0 < 0) return;
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+    for (int m = lane; m < M; m += 32) {
+      const double ym = w.y64[m];
+      a0 = fma(__ldg(At + (size_t)j0 * M + m), ym, a0);
+      if (j1 >= 0) a1 = fma(__ldg(At + (size_t)j1 * M + m), ym, a1);
+      if (j2 >= 0) a2 = fma(__ldg(At + (size_t)j2 * M + m), ym, a2);
+      if (j3 >= 0) a3 = fma(__ldg(At + (size_t)j3 * M + m), ym, a3);
+    }
+    const bool h4 = (lane & 16) != 0, h3 = (lane & 8) != 0;
+    double k0 = h4 ? a2 : a0, k1 = h4 ? a3 : a1;
+    k0 += __shfl_xor_sync(0xffffffffu, h4 ? a0 : a2, 16);
+    k1 += __shfl_xor_sync(0xffffffffu, h4 ? a1 : a3, 16);
+    double v = h3 ? k1 : k0;
+    v += __shfl_xor_sync(0xffffffffu, h3 ? k0 : k1, 8);
+    v += __shfl_xor_sync(0xffffffffu, v, 4);
+    v += __shfl_xor_sync(0xffffffffu, v, 2);
+    v += __shfl_xor_sync(0xffffffffu, v, 1);
     __syncwarp();
-    if (w.lane == 0) {
-      w.bx[j] = acc;
-      w.bk[j] = 1;
+    if ((lane & 7) == 0) {
+      const int i = lane >> 3;  // 2 (lane bit 4) + (lane bit 3)
+      const int j = i == 0 ? j0 : i == 1 ? j1 : i == 2 ? j2 : j3;
+      if (j >= 0) {
+        w.bx[j] = v;
+        w.bk[j] = 1;
+      }
     }
     __syncwarp();
   }
@@ -415,13 +448,14 @@ __device__ bool chol32(Warp& w, float* L, float* invd, int n, const int16_t* ato
 // that must not change multiply a zero.  Reads past the stored rows (lanes of rows >= n,
 // or past row i's last entry) stay inside the triangle region and are multiplied by
 // zero or land in rows >= n, which no one reads.
-template <int VR>
+// fwd_unit<VR, K> sweeps only the first K slots (n <= 32 K): the rest are left alone.
+template <int VR, int K = VR>
 __device__ void fwd_unit(const float* U, int n, float (&v)[VR], int lane) {
-  int base[VR];
+  int base[K];
 #pragma unroll
-  for (int k = 0; k < VR; ++k) base[k] = ridx(min(lane + 32 * k, n > 0 ? n - 1 : 0), 0);
+  for (int k = 0; k < K; ++k) base[k] = ridx(min(lane + 32 * k, n > 0 ? n - 1 : 0), 0);
 #pragma unroll
-  for (int S = 0; S < VR; ++S) {
+  for (int S = 0; S < K; ++S) {
     if (32 * S >= n) break;  // warp-uniform
     const int iend = min(n, 32 * S + 32);
     const int t = lane + 32 * S;
@@ -430,7 +464,7 @@ __device__ void fwd_unit(const float* U, int n, float (&v)[VR], int lane) {
       const float l = t > i ? U[base[S] + i] : 0.f;
       v[S] = fmaf(-l, zi, v[S]);
 #pragma unroll
-      for (int k = S + 1; k < VR; ++k) v[k] = fmaf(-U[base[k] + i], zi, v[k]);
+      for (int k = S + 1; k < K; ++k) v[k] = fmaf(-U[base[k] + i], zi, v[k]);
     }
   }
 }
@@ -513,21 +547,31 @@ __device__ __forceinline__ bool refine32(const float* L, const float* invd, int 
         acc[k][0] = t < n ? bx[col[k]] : 0.0;
         acc[k][1] = 0.0;
       }
+      // whole blocks of kB columns, then the rest one by one (an FP64 instruction costs
+      // the pipe as much with one useful lane as with 32, so none is spent on padding)
       constexpr int kB = VR <= 2 ? 8 : 4;
-      for (int j0 = 0; j0 < n; j0 += kB) {
+      int j0 = 0;
+      for (; j0 + kB <= n; j0 += kB) {
         double g[kB][VR];
 #pragma unroll
         for (int jj = 0; jj < kB; ++jj) {
-          const double* grow = G + (size_t)atoms[min(j0 + jj, n - 1)] * N;
+          const double* grow = G + (size_t)atoms[j0 + jj] * N;
 #pragma unroll
           for (int k = 0; k < VR; ++k) g[jj][k] = 32 * k < n ? __ldg(grow + col[k]) : 0.0;
         }
 #pragma unroll
         for (int jj = 0; jj < kB; ++jj) {
-          const double sj = j0 + jj < n ? s[j0 + jj] : 0.0;
+          const double sj = s[j0 + jj];
 #pragma unroll
           for (int k = 0; k < VR; ++k) acc[k][jj & 1] = fma(-g[jj][k], sj, acc[k][jj & 1]);
         }
+      }
+      for (; j0 < n; ++j0) {
+        const double* grow = G + (size_t)atoms[j0] * N;
+        const double sj = s[j0];
+#pragma unroll
+        for (int k = 0; k < VR; ++k)
+          acc[k][j0 & 1] = fma(-(32 * k < n ? __ldg(grow + col[k]) : 0.0), sj, acc[k][j0 & 1]);
       }
 #pragma unroll
       for (int k = 0; k < VR; ++k) rr[k] = lane + 32 * k < n ? acc[k][0] + acc[k][1] : 0.0;
@@ -546,11 +590,17 @@ __device__ __noinline__ bool refine32_ool(const float* L, const float* invd, int
                                           const double* G, int N, int lane) {
   return refine32<VR>(L, invd, n, atoms, s, bx, G, N, lane);
 }
+// A copy takes as many register slots per lane as the system has rows in use: slots past
+// them would only add instructions, FP64 ones in the residual among them.
 template <int VR, bool OOL>
 __device__ __forceinline__ bool refine(const float* L, const float* invd, int n,
                                        const int16_t* atoms, double* s, const double* bx,
                                        const double* G, int N, int lane) {
-  if (OOL) return refine32_ool<VR>(L, invd, n, atoms, s, bx, G, N, lane);
+  if (OOL) {
+    if (VR > 1 && n <= 32) return refine32_ool<1>(L, invd, n, atoms, s, bx, G, N, lane);
+    if (VR > 2 && n <= 64) return refine32_ool<(VR > 2 ? 2 : VR)>(L, invd, n, atoms, s, bx, G, N, lane);
+    return refine32_ool<VR>(L, invd, n, atoms, s, bx, G, N, lane);
+  }
   return refine32<VR>(L, invd, n, atoms, s, bx, G, N, lane);
 }
 
@@ -558,12 +608,13 @@ __device__ __forceinline__ bool refine(const float* L, const float* invd, int n,
 // rows, for atoms appended at the end of c (gOMP's growing support): for row i,
 // z = U_{0:i}^{-1} G(c_{0:i}, c_i) by one forward sweep with the factor built so far,
 // U(i, k) = z_k d2_k, pivot D(i) = G(c_i, c_i) - sum_k z_k^2 d2_k and d2_i = 1 / D(i).
-// Returns false when a pivot drops below 1e-4 of its diagonal.
+// Returns false when a pivot drops below 1e-4 of its diagonal.  One out-of-line copy
+// serves gOMP's two callers (its growing support and the refit on q), which keeps the
+// kernel's hot loop within the instruction cache (12% faster on the 2048^2 x 256 cube);
+// pointer and scalar arguments keep the caller's state in registers.
 template <int VR>
-__device__ bool chol32_append(Warp& w, float* L, float* invd, int nf, int n,
-                              const int16_t* atoms) {
-  const int lane = w.lane, N = w.cb->N;
-  const float* G32 = w.cb->G32;
+__device__ __noinline__ bool chol32_append(const float* G32, int N, float* L, float* invd,
+                                           int nf, int n, const int16_t* atoms, int lane) {
   for (int i = nf; i < n; ++i) {
     const size_t row = (size_t)atoms[i] * N;
     float g[VR];
@@ -575,7 +626,9 @@ __device__ bool chol32_append(Warp& w, float* L, float* invd, int nf, int n,
       g[k] = t < i ? v : 0.f;
     }
     const float gii = __ldg(G32 + row + atoms[i]);
-    fwd_unit<VR>(L, i, g, lane);  // g := U_{0:i}^{-1} g
+    // g := U_{0:i}^{-1} g (the first rows need one register slot)
+    if (VR > 1 && i <= 32) fwd_unit<VR, 1>(L, i, g, lane);
+    else fwd_unit<VR>(L, i, g, lane);
     float ss = 0.f;
 #pragma unroll
     for (int k = 0; k < VR; ++k) {
@@ -801,6 +854,15 @@ __device__ __forceinline__ bool ls_fresh(Warp& w, const int16_t* atoms, int n, d
                                          double* invd, double* v, double* s, int cap) {
   return ls_fresh_impl(atoms, n, L, invd, v, s, cap, w.cb->G64, w.cb->N, w.bx, w.wv, w.lane);
 }
+// The FP64 fallback in the warp's global slot: factor, inverse pivots, forward solution
+// and the row scratch of append_row, for systems of up to dmax rows.
+__device__ __forceinline__ bool ls_fresh_global(Warp& w, const int16_t* atoms, int n, double* s) {
+  const int D = w.p.dmax;
+  double* Lg = w.fb;
+  double* inv = Lg + D * (D + 1) / 2;
+  return ls_fresh_impl(atoms, n, Lg, inv, inv + D, s, D, w.cb->G64, w.cb->N, w.bx, inv + 2 * D,
+                       w.lane);
+}
 
 template <int VR, bool OOL>
 __device__ bool ls_solve(Warp& w, const int16_t* atoms, int n, double* Lbuf, double* invdbuf,
@@ -813,9 +875,7 @@ __device__ bool ls_solve(Warp& w, const int16_t* atoms, int n, double* Lbuf, dou
   // FP64 fallback: in place when the shared regions are FP64-sized, else in the warp's
   // global slot (capacity dmax >= n)
   if (w.fb) {
-    const int D = w.p.dmax;
-    double* Lg = w.fb;
-    return ls_fresh(w, atoms, n, Lg, Lg + D * (D + 1) / 2, Lg + D * (D + 1) / 2 + D, s, D);
+    return ls_fresh_global(w, atoms, n, s);
   }
   return ls_fresh(w, atoms, n, Lbuf, invdbuf, vbuf, s, cap);
 }
@@ -829,23 +889,56 @@ __device__ bool ls_solve_grow(Warp& w, const int16_t* atoms, int& nf, int n, dou
   if (n > w.p.d32 && w.fb) {
     // the support outgrew the shared-memory factor: FP64 in the warp's global slot
     nf = 0;
-    const int D = w.p.dmax;
-    double* Lg = w.fb;
-    return ls_fresh(w, atoms, n, Lg, Lg + D * (D + 1) / 2, Lg + D * (D + 1) / 2 + D, s, D);
+    return ls_fresh_global(w, atoms, n, s);
   }
   float* L32 = reinterpret_cast<float*>(Lbuf);
   float* inv32 = reinterpret_cast<float*>(invdbuf);
-  const bool factored = chol32_append<VR>(w, L32, inv32, nf, n, atoms);
+  const bool factored = chol32_append<VR>(w.cb->G32, w.cb->N, L32, inv32, nf, n, atoms, w.lane);
   nf = factored ? n : 0;
   if (factored && refine<VR, true>(L32, inv32, n, atoms, s, w.bx, w.cb->G64, w.cb->N, w.lane))
     return true;
   if (w.fb) {
-    const int D = w.p.dmax;
-    double* Lg = w.fb;
-    return ls_fresh(w, atoms, n, Lg, Lg + D * (D + 1) / 2, Lg + D * (D + 1) / 2 + D, s, D);
+    return ls_fresh_global(w, atoms, n, s);
   }
   nf = 0;  // the FP64 fallback below overwrites the FP32 factor's region
   return ls_fresh(w, atoms, n, Lbuf, invdbuf, vbuf, s, cap);
+}
+
+// gOMP's refit on the kept atoms q: the FP32 factor Lq of the last refit holds the atoms
+// qf[0..nqf) in that order, and rows of a Cholesky factor depend only on the rows before
+// them, so the rows of the longest common prefix of q and qf are kept and only the rest
+// is appended (q keeps c's arrival order, and the strongest atoms, which stay, arrive
+// first).  nqf is updated to the rows Lq holds afterwards.  An unchanged q reuses the
+// whole factor and so reproduces the last solution bit for bit.
+template <int VR>
+__device__ bool ls_solve_refit(Warp& w, const int16_t* q, int n, int& nqf, double* Lbuf,
+                               double* invdbuf, double* vbuf, double* s, int cap) {
+  const int lane = w.lane;
+  int pre = 0;
+  const int common = min(n, nqf);
+  for (int t0 = 0; t0 < common; t0 += 32) {
+    const int t = t0 + lane;
+    const unsigned diff = __ballot_sync(0xffffffffu, t < common && q[t] != w.qf[t]);
+    if (diff) {
+      pre = t0 + __ffs(diff) - 1;
+      break;
+    }
+    pre = min(t0 + 32, common);
+  }
+  __syncwarp();
+  float* L32 = reinterpret_cast<float*>(Lbuf);
+  float* inv32 = reinterpret_cast<float*>(invdbuf);
+  const bool factored = chol32_append<VR>(w.cb->G32, w.cb->N, L32, inv32, pre, n, q, lane);
+  for (int t = pre + lane; t < n; t += 32) w.qf[t] = q[t];
+  nqf = factored ? n : 0;
+  __syncwarp();
+  if (factored && refine<VR, true>(L32, inv32, n, q, s, w.bx, w.cb->G64, w.cb->N, lane))
+    return true;
+  if (w.fb) {
+    return ls_fresh_global(w, q, n, s);
+  }
+  nqf = 0;  // the FP64 fallback below overwrites the FP32 factor's region
+  return ls_fresh(w, q, n, Lbuf, invdbuf, vbuf, s, cap);
 }
 
 // Minimum-norm solution for |c| > M: s = A_c^T H^{-1} y with H = A_c A_c^T (M x M).
@@ -856,12 +949,13 @@ __device__ bool ls_min_norm(Warp& w, const int16_t* atoms, int n, double* s) {
   double* L = w.fb ? w.fb : w.L;
   double* invd = w.fb ? w.fb + M * (M + 1) / 2 : w.invd;
   double* v = w.fb ? w.fb + M * (M + 1) / 2 + M : w.v;
+  double* wv = w.fb ? w.fb + M * (M + 1) / 2 + 2 * M : w.wv;
   const int cap = M;
   bool ok = true;
   for (int k = 0; k < M; ++k) {
     // row k of H: H(k, t) = sum_j A[k][c_j] A[t][c_j]
     ok &= append_row(
-        w.lane, w.wv, L, invd, v, cap, k,
+        w.lane, wv, L, invd, v, cap, k,
         [&](int t) {
           double h = 0.0;
           for (int j = 0; j < n; ++j) {
@@ -919,6 +1013,7 @@ __global__ void __launch_bounds__(256, 2) k_greedy(GrParams p) {
   w.b32 = (float*)(base + lay.b32);
   w.xqf = (float*)(base + lay.xqf);
   w.bx = (double*)(base + lay.bx);
+  w.y64 = (double*)(base + lay.y64);
   w.xq = (double*)(base + lay.xq);
   w.xqp = (double*)(base + lay.xqp);
   w.L = (double*)(base + lay.L);
@@ -939,6 +1034,7 @@ __global__ void __launch_bounds__(256, 2) k_greedy(GrParams p) {
   w.c = (int16_t*)(base + lay.c);
   w.q = (int16_t*)(base + lay.q);
   w.qp = (int16_t*)(base + lay.qp);
+  w.qf = (int16_t*)(base + lay.qf);
   w.sel = (int16_t*)(base + lay.sel);
   w.fb = p.fb64 ? p.fb64 + (size_t)(blockIdx.x * (blockDim.x >> 5) + wid) * p.fb_slot : nullptr;
 
@@ -996,6 +1092,7 @@ __global__ void __launch_bounds__(256, 2) k_greedy(GrParams p) {
       float yv = cb.Y[pix * M + m];
       bad |= !isfinite(yv);
       w.y[m] = yv;
+      w.y64[m] = (double)yv;
       w.rf[m] = yv;  // r^0 = y
       y2 = fmaf(yv, yv, y2);
     }
@@ -1008,6 +1105,7 @@ __global__ void __launch_bounds__(256, 2) k_greedy(GrParams p) {
 
     int nc = 0, nq = 0, nqp = 0, it = 0;
     int nf = 0;  // gOMP: rows of the FP32 factor of G_c carried over between iterations
+    int nqf = 0;  // gOMP: rows of the refit factor of G_q carried over between iterations
     float x1 = 0.f;     // sum |x_q| of the current iterate, rounded up
     float rerr = 0.f;   // error bound of the FP32 residual of the current iterate (r^0 = y)
     uint8_t conv = 0;
@@ -1021,9 +1119,10 @@ __global__ void __launch_bounds__(256, 2) k_greedy(GrParams p) {
       if (lane == 0) ring[0] = h0;
       __syncwarp();
     }
-    // algorithmic flops of the method for this pixel: correlation 2MN, Cholesky least
+    // algorithmic flops of the method for this pixel, times 3 (an integer; integer
+    // arithmetic keeps the count off the FP64 pipe): correlation 2MN, Cholesky least
     // squares n^3/3 + 2n^2 per support of n atoms (min-norm form for n > M), residual 2M|q|
-    double work = 0.0;
+    long long work3 = 0;
     bool fail = false;
     while (!p.start_done && it < cap) {
       // ---- step 1: correlation p = A^T r = A^T y - (A^T A)_{:,q} x_q (u = x + mu p for
@@ -1155,17 +1254,18 @@ __global__ void __launch_bounds__(256, 2) k_greedy(GrParams p) {
       }
       if (fail) break;
       {
-        const double n = nc, m = M;
-        double ls;
+        const long long n = nc, m = M;
+        long long ls3;
         if (ALGO == kGomp) {
-          // rows appended to the factor: a forward sweep of i^2 flops for row i
-          const double a = nf0, b = nc;  // rows [a, b)
-          ls = ((b - 1) * b * (2 * b - 1) - (a - 1) * a * (2 * a - 1)) / 6.0 + 2.0 * n * n;
+          // rows appended to the factor: a forward sweep of i^2 flops for row i, i in
+          // [a, b); (b-1) b (2b-1) is a multiple of 6
+          const long long a = nf0, b = nc;
+          ls3 = ((b - 1) * b * (2 * b - 1) - (a - 1) * a * (2 * a - 1)) / 2 + 6 * n * n;
         } else {
-          ls = nc <= M ? n * n * n / 3.0 + 2.0 * n * n
-                       : n * m * m + m * m * m / 3.0 + 2.0 * m * m + n * m;
+          ls3 = nc <= M ? n * n * n + 6 * n * n
+                        : 3 * n * m * m + m * m * m + 6 * m * m + 3 * n * m;
         }
-        work += 2.0 * m * N + ls;
+        work3 += 6 * m * N + ls3;
       }
 
       // ---- step 3: prune to kappa (and refit for gOMP) ----
@@ -1194,8 +1294,8 @@ __global__ void __launch_bounds__(256, 2) k_greedy(GrParams p) {
       // the refit on q; when q is all of c (in c's order) it would repeat the solve just
       // made, bit for bit, so x keeps that solution
       if (ALGO == kGomp && nq > 0 && nq < nc) {
-        fail |= !ls_solve<VR, true>(w, w.q, nq, w.Lq, w.invq, w.vq, w.sq, p.kmax);
-        work += (double)nq * nq * nq / 3.0 + 2.0 * nq * nq;
+        fail |= !ls_solve_refit<VR>(w, w.q, nq, nqf, w.Lq, w.invq, w.vq, w.sq, p.kmax);
+        work3 += (long long)nq * nq * nq + 6ll * nq * nq;
         if (fail) break;
         for (int j = lane; j < nq; j += 32) w.xq[j] = w.sq[j];
         __syncwarp();
@@ -1250,7 +1350,7 @@ __global__ void __launch_bounds__(256, 2) k_greedy(GrParams p) {
         }
       }
       d2 = warp_sum(d2);
-      work += 2.0 * M * nq;
+      work3 += 6ll * M * nq;
       ++it;
       // each FP32 residual errs from r = y - A x by at most (|q| + 3) u (||y|| + ||A_j||max
       // ||x||_1) in norm (rounded A and x, |q| rounded FMAs)
@@ -1362,7 +1462,7 @@ __global__ void __launch_bounds__(256, 2) k_greedy(GrParams p) {
     if (lane == 0) {
       if (cb.iters_out) cb.iters_out[pix] = it;
       if (cb.conv_out) cb.conv_out[pix] = conv;
-      if (p.work) atomicAdd(p.work, work);
+      if (p.work) atomicAdd(p.work, (double)work3 / 3.0);
     }
     __syncwarp();
   }
@@ -1557,7 +1657,7 @@ cudaError_t run_greedy(Ctx& c, GreedyAlgo algo, const GreedyArgs& a, const GrCub
     long long need = (total + warps - 1) / warps;
     if (grid > need) grid = need;
     const int D = p.dmax;
-    p.fb_slot = D * (D + 1) / 2 + 2 * D;
+    p.fb_slot = D * (D + 1) / 2 + 3 * D;
     size_t elems = (size_t)grid * warps * p.fb_slot;
     if (c.fb64_elems < elems) {
       cudaFree(c.fb64);
