@@ -130,7 +130,10 @@ cs_status cs_get_lipschitz(const cs_ctx *ctx, double *L);
 cs_status cs_get_dictionary(const cs_ctx *ctx, double *A_host);
 
 /* Measurement, Eq. 1: Y[p] = A X[p] (+ E[p]) for p < P.  X: P x N, Y: P x M, E: P x M
- * additive noise or NULL (the same kind of memory as X and Y).  FP32 arithmetic. */
+ * additive noise or NULL (the same kind of memory as X and Y).  FP32 arithmetic.  A
+ * cube in host memory is measured in chunks of 262,144 pixels whose copies in and out
+ * overlap the kernel (pinned memory lets them); the results equal a device-memory
+ * call's bit for bit. */
 cs_status cs_measure(cs_ctx *ctx, const float *X, float *Y, const float *E, int64_t P);
 
 /* FISTA, Algorithm 1: x^0 = z^0 = 0, t^0 = 1; per iteration

@@ -197,6 +197,56 @@ cs_status with_cube(cs_ctx* ctx, const float* Y, float* X, int64_t P, int in_col
   return CS_OK;
 }
 
+// Eq. 1 on a cube in host memory, in chunks of up to kHostChunk pixels: while chunk k is
+// measured, chunk k + 1 (X and E) is copied in and chunk k - 1 (Y) copied out, through
+// two device buffers per direction (the context's pipeline buffers; E's in stage_aux).
+// Every pixel is computed by the same kernel as in a device-memory call, so the results
+// are the same bit for bit.
+constexpr int64_t kHostChunk = 262144;
+cs_status measure_host(Ctx& c, const float* X, float* Y, const float* E, int64_t P) {
+  const int64_t C = std::min(kHostChunk, P);
+  cudaError_t e = ensure_aux(c);
+  if (e == cudaSuccess) e = ensure_pipe(c, C);
+  if (e == cudaSuccess && E)
+    e = ensure_stage(&c.stage_aux, &c.stage_aux_bytes, sizeof(float) * 2 * (size_t)C * c.M);
+  if (e != cudaSuccess) return cuda_fail(e, "stream buffers");
+  e = cudaEventRecord(c.ev_fork, c.stream);
+  for (int k = 0; k < 3 && e == cudaSuccess; ++k) e = cudaStreamWaitEvent(c.aux[k], c.ev_fork, 0);
+  if (e != cudaSuccess) return cuda_fail(e, "stream fork");
+  cudaStream_t s_in = c.aux[0], s_out = c.aux[1], s_comp = c.aux[2], own = c.stream;
+  int64_t off = 0;
+  for (int k = 0; off < P && e == cudaSuccess; ++k, off += C) {
+    const int b = k & 1;
+    const int64_t n = std::min(C, P - off);
+    float* Eb = E ? c.stage_aux + (size_t)b * C * c.M : nullptr;
+    if (k >= 2) e = cudaStreamWaitEvent(s_in, c.ev_out[b], 0);  // buffer b copied out
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(c.pipe_x[b], X + off * c.N, sizeof(float) * n * c.N,
+                          cudaMemcpyHostToDevice, s_in);
+    if (e == cudaSuccess && E)
+      e = cudaMemcpyAsync(Eb, E + off * c.M, sizeof(float) * n * c.M, cudaMemcpyHostToDevice,
+                          s_in);
+    if (e == cudaSuccess) e = cudaEventRecord(c.ev_in[b], s_in);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s_comp, c.ev_in[b], 0);
+    if (e != cudaSuccess) break;
+    c.stream = s_comp;
+    e = launch_measure(c, c.pipe_x[b], c.pipe_y[b], Eb, n);
+    c.stream = own;
+    if (e == cudaSuccess) e = cudaEventRecord(c.ev_comp[b], s_comp);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s_out, c.ev_comp[b], 0);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(Y + off * c.M, c.pipe_y[b], sizeof(float) * n * c.M,
+                          cudaMemcpyDeviceToHost, s_out);
+    if (e == cudaSuccess) e = cudaEventRecord(c.ev_out[b], s_out);
+  }
+  cudaError_t ej = cudaEventRecord(c.ev_join[1], s_out);
+  if (ej == cudaSuccess) ej = cudaStreamWaitEvent(c.stream, c.ev_join[1], 0);
+  if (e == cudaSuccess) e = ej;
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c.stream);
+  if (e != cudaSuccess) return cuda_fail(e, "streamed measurement");
+  return CS_OK;
+}
+
 }  // namespace
 }  // namespace cs
 
@@ -345,19 +395,13 @@ cs_status cs_measure(cs_ctx* ctx, const float* X, float* Y, const float* E, int6
   if (P == 0) return CS_OK;
   if (!X || !Y) return arg_error("X or Y is NULL");
   cs::Ctx& c = ctx->c;
-  const float* Ed = E;
   if (E && cs::is_device_ptr(E) != cs::is_device_ptr(X))
     return arg_error("E must be the same kind of memory as X and Y");
-  if (E && !cs::is_device_ptr(E)) {  // host noise: staged like the cube
-    size_t bytes = sizeof(float) * (size_t)P * c.M;
-    cudaError_t e = cs::ensure_stage(&c.stage_aux, &c.stage_aux_bytes, bytes);
-    if (e != cudaSuccess) return cuda_fail(e, "staging allocation");
-    e = cudaMemcpyAsync(c.stage_aux, E, bytes, cudaMemcpyHostToDevice, c.stream);
-    if (e != cudaSuccess) return cuda_fail(e, "host-to-device copy");
-    Ed = c.stage_aux;
-  }
+  if (cs::is_device_ptr(X) != cs::is_device_ptr(Y))
+    return arg_error("input and output must both be device or both be host memory");
+  if (!cs::is_device_ptr(X)) return cs::measure_host(c, X, Y, E, P);  // copies overlapped
   return cs::with_cube(ctx, X, Y, P, c.N, c.M, [&](const float* Xd, float* Yd) {
-    return cs::launch_measure(c, Xd, Yd, Ed, P);
+    return cs::launch_measure(c, Xd, Yd, E, P);
   });
 }
 

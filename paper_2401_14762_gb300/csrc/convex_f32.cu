@@ -479,6 +479,155 @@ __global__ void __launch_bounds__(kThreads, 1) k_measure_f32(CvParams p) {
   }
 }
 
+// ---------------------------------------------------------------------------------
+// Eq. 1 measurement for N a multiple of 4: Y = X A^T (+ E) as a register-tiled SIMT
+// product.  Persistent CTAs of 256 threads walk tiles of 256 pixels; A (rows padded to
+// 16 RM with zeros, columns to a multiple of 32) stays in shared memory, and the tile's X
+// arrives in chunks of 32 columns through a cp.async ring (3 stages, 2 when A is large),
+// so the next chunks stream from HBM while the current one is multiplied.  Thread
+// (tp, tm) of the 16 x 16 grid owns pixels 16 tp .. 16 tp + 15 and rows tm + 16 r
+// (r < RM): per float4 step of k it reads 16 float4 of X and RM of A for 64 RM FMAs, so
+// shared memory (one 8-lane wavefront per cycle) keeps up with the FMA pipes.  Each
+// output is summed in the order k = 0, 1, ..., N-1.
+// ---------------------------------------------------------------------------------
+struct MtParams {
+  int M, N, lda;   // lda: row stride of A in shared memory
+  const float* A;  // M x N global
+  const float* X;  // P x N
+  const float* E;  // P x M or null
+  float* Y;        // P x M
+  int64_t P;
+};
+
+constexpr int kMtP = 256;            // pixels per tile
+constexpr int kMtPx = kMtP / 16;     // pixels per thread
+constexpr int kMtK = 32;             // columns per chunk
+constexpr int kMtLdx = kMtK + 4;     // row stride of a staged X chunk (16-byte rows)
+// stages of the X ring beside A (16 RM rows of lda floats)
+__host__ __device__ constexpr int mt_stages(int rm, int lda) {
+  return 4 * (16 * rm * lda + 3 * kMtP * kMtLdx) <= 227 * 1024 ? 3 : 2;
+}
+
+__device__ __forceinline__ void cp_async16(float* dst, const float* src, bool valid) {
+  const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(dst));
+  const int n = valid ? 16 : 0;  // 0: the 16 bytes are zero-filled, nothing is read
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(src), "r"(n)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+template <int RM, int ST>
+__global__ void __launch_bounds__(256, 1) k_measure_tiled(MtParams p) {
+  extern __shared__ __align__(16) float sm[];
+  const int M = p.M, N = p.N, lda = p.lda;
+  float* As = sm;                 // 16 RM x lda
+  float* Xs = As + 16 * RM * lda; // kMtStages x kMtP x kMtLdx
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int tm = lane & 15, tp = (lane >> 4) + 2 * warp;
+  for (int i = tid; i < 16 * RM * lda; i += 256) {
+    const int r = i / lda, c = i - r * lda;
+    As[i] = (r < M && c < N) ? p.A[(size_t)r * N + c] : 0.f;
+  }
+  const int nch = (N + kMtK - 1) / kMtK;
+  const int64_t ntiles = (p.P + kMtP - 1) / kMtP;
+  const int64_t my_tiles = ntiles > blockIdx.x ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+  const int64_t items = my_tiles * nch;  // (tile, chunk) pairs of this CTA, in order
+  // thread tid copies float4 j of the chunk: pixel (tid + 256 j) / 8, column group % 8
+  auto issue = [&](int64_t it) {
+    if (it < items) {
+      const int64_t tile = blockIdx.x + (it / nch) * gridDim.x;
+      const int ch = (int)(it % nch);
+      float* dst = Xs + (size_t)(it % ST) * kMtP * kMtLdx;
+#pragma unroll
+      for (int j = 0; j < kMtP * kMtK / 4 / 256; ++j) {
+        const int idx = tid + 256 * j, px = idx >> 3, k4 = idx & 7;
+        const int64_t pix = tile * kMtP + px;
+        const int col = ch * kMtK + 4 * k4;
+        const bool ok = pix < p.P && col < N;
+        cp_async16(dst + px * kMtLdx + 4 * k4, ok ? p.X + pix * N + col : p.X, ok);
+      }
+    }
+    cp_async_commit();  // one group per item, empty past the end, so the counts stay aligned
+  };
+#pragma unroll
+  for (int s = 0; s < ST - 1; ++s) issue(s);
+  float acc[kMtPx][RM];
+#pragma unroll
+  for (int i = 0; i < kMtPx; ++i)
+#pragma unroll
+    for (int r = 0; r < RM; ++r) acc[i][r] = 0.f;
+  for (int64_t it = 0; it < items; ++it) {
+    cp_async_wait<ST - 2>();
+    __syncthreads();  // chunk it is in place; every thread is done with chunk it - 1
+    issue(it + ST - 1);
+    const float* xb = Xs + (size_t)(it % ST) * kMtP * kMtLdx + (kMtPx * tp) * kMtLdx;
+    const int ch = (int)(it % nch);
+    const float* ab = As + tm * lda + ch * kMtK;
+#pragma unroll 1
+    for (int k4 = 0; k4 < kMtK / 4; ++k4) {
+      float4 xv[kMtPx];
+#pragma unroll
+      for (int i = 0; i < kMtPx; ++i)
+        xv[i] = *reinterpret_cast<const float4*>(xb + i * kMtLdx + 4 * k4);
+#pragma unroll
+      for (int r = 0; r < RM; ++r) {
+        const float4 a = *reinterpret_cast<const float4*>(ab + 16 * r * lda + 4 * k4);
+#pragma unroll
+        for (int i = 0; i < kMtPx; ++i) {
+          float t = fmaf(xv[i].x, a.x, acc[i][r]);
+          t = fmaf(xv[i].y, a.y, t);
+          t = fmaf(xv[i].z, a.z, t);
+          acc[i][r] = fmaf(xv[i].w, a.w, t);
+        }
+      }
+    }
+    if (ch == nch - 1) {  // the tile is complete: add E, store, restart the sums
+      const int64_t tile = blockIdx.x + (it / nch) * gridDim.x;
+#pragma unroll
+      for (int i = 0; i < kMtPx; ++i) {
+        const int64_t pix = tile * kMtP + kMtPx * tp + i;
+#pragma unroll
+        for (int r = 0; r < RM; ++r) {
+          const int m = tm + 16 * r;
+          if (pix < p.P && m < M) {
+            const int64_t o = pix * M + m;
+            p.Y[o] = acc[i][r] + (p.E ? p.E[o] : 0.f);
+          }
+          acc[i][r] = 0.f;
+        }
+      }
+    }
+  }
+  cp_async_wait<0>();
+}
+
+template <int RM, int ST>
+static cudaError_t measure_tiled_st(const Ctx& c, MtParams p, size_t smem) {
+  cudaError_t e = cudaFuncSetAttribute(k_measure_tiled<RM, ST>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const int64_t ntiles = (p.P + kMtP - 1) / kMtP;
+  const int64_t grid = ntiles < c.num_sms ? ntiles : c.num_sms;
+  k_measure_tiled<RM, ST><<<(unsigned)grid, 256, smem, c.stream>>>(p);
+  return cudaGetLastError();
+}
+
+template <int RM>
+static cudaError_t measure_tiled(const Ctx& c, MtParams p) {
+  const int kpad = (c.N + kMtK - 1) / kMtK * kMtK;
+  p.lda = kpad + 4;  // 16-byte rows; 8 consecutive rows fall on distinct 4-bank groups
+  const int st = mt_stages(RM, p.lda);
+  const size_t smem = sizeof(float) * ((size_t)16 * RM * p.lda + (size_t)st * kMtP * kMtLdx);
+  if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
+  return st == 3 ? measure_tiled_st<RM, 3>(c, p, smem) : measure_tiled_st<RM, 2>(c, p, smem);
+}
+
 // Momentum weights of Algorithm 1 steps 3-4: t_0 = 1, t_i = (1 + sqrt(1 + 4 t_{i-1}^2)) / 2,
 // beta_i = (t_{i-1} - 1) / t_i, in FP64 by one thread (the sequence is the same for all
 // pixels), stored as FP32 for the iteration kernels.
@@ -643,6 +792,19 @@ cudaError_t launch_measure(const Ctx& c, const float* X, float* Y, const float* 
   p.E = E;
   p.P = P;
   if (P == 0) return cudaSuccess;
+  if (c.N % 4 == 0 && c.M <= 128 && (reinterpret_cast<uintptr_t>(X) & 15) == 0) {
+    MtParams q{c.M, c.N, 0, c.A32, X, E, Y, P};
+    switch ((c.M + 15) / 16) {
+      case 1: return measure_tiled<1>(c, q);
+      case 2: return measure_tiled<2>(c, q);
+      case 3: return measure_tiled<3>(c, q);
+      case 4: return measure_tiled<4>(c, q);
+      case 5: return measure_tiled<5>(c, q);
+      case 6: return measure_tiled<6>(c, q);
+      case 7: return measure_tiled<7>(c, q);
+      default: return measure_tiled<8>(c, q);
+    }
+  }
   int mr = (c.M + 31) / 32;
   if (mr == 1) return measure_mr<1>(c, p);
   if (mr == 2) return measure_mr<2>(c, p);

@@ -58,8 +58,11 @@ def test_setup_given_A_and_Psi(cs):
 # --------------------------------------------------------------------------- measure
 @pytest.mark.parametrize("M,N", [(48, 120), (80, 200), (102, 256), (128, 256), (3, 5)])
 def test_measure(cs, M, N):
+    """Y = X A^T + E per pixel, to FP32 accuracy.  P spans two or three 256-pixel tiles
+    per CTA of the persistent tiled kernel (N a multiple of 4) and ends on a ragged tile;
+    N = 5 takes the general kernel."""
     torch = pytest.importorskip("torch")
-    P = 32 * 5 + 3
+    P = 256 * 152 * 2 + 37
     Phi = sy.gaussian_phi(M, N, 3)
     A = orc.dictionary(Phi)
     X = sy.powerlaw_coeffs(P, N, 3, permute=True).astype(np.float32)

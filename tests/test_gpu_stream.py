@@ -100,3 +100,27 @@ def test_stream_argument_errors(cs):
             cs.cs_recover_stream(ctx, cs.CS_ALGO_COSAMP, *args, **kw)
         assert e.value.status == cs.CS_ERR_ARG
     cs.cs_recover_stream(ctx, cs.CS_ALGO_COSAMP, Y[:0], X[:0], 4, kappa=5)  # P = 0
+
+
+@pytest.mark.parametrize("pinned", [True, False])
+def test_measure_host_cube_is_chunked_bit_for_bit(cs, pinned):
+    """cs_measure on a host-memory cube runs in chunks of 262,144 pixels with the copies
+    overlapped: Y equals the device-memory call's bit for bit, over two whole chunks and a
+    ragged third, with and without E."""
+    torch = torch_cuda()
+    M, N, P = 48, 120, 2 * 262144 + 777
+    Phi = sy.gaussian_phi(M, N, 5)
+    ctx = cs.cs_create(M, N, Phi=Phi)
+    X = torch.from_numpy(sy.sparse_coeffs(P, N, 6, 5)).float()
+    E = torch.from_numpy(sy.noise(P, M, 1e-3, 5)).float()
+    if pinned:
+        X, E = X.pin_memory(), E.pin_memory()
+    for noise in (E, None):
+        Yd = torch.empty((P, M), device="cuda")
+        cs.cs_measure(ctx, X.cuda(), Yd, None if noise is None else noise.cuda())
+        cs.cs_sync(ctx)
+        Yh = torch.full((P, M), float("nan"))
+        if pinned:
+            Yh = Yh.pin_memory()
+        cs.cs_measure(ctx, X, Yh, noise)
+        assert torch.equal(Yh, Yd.cpu())
