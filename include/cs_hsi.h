@@ -156,8 +156,10 @@ cs_status cs_recover_fista(cs_ctx *ctx, const float *Y, float *X, int64_t P, dou
  * The x-update runs as h = W (y - A d), x = d + A^T h with d = z - w and
  * W = (A A^T + rho I)^{-1} factored once in FP64.  prec = CS_BF16 runs its three
  * products on the tensor cores with split-BF16 operands (about 16 bits each, FP32
- * accumulation) where the 128-pixel tile fits in shared memory (for example N = 200,
- * M = 80); other shapes use the FP32 path. */
+ * accumulation) for the same (N, M) shapes as FISTA's: N and M padded to 16 of (128, 48),
+ * (208, 80), (224, 96) or (256, 112).  Other shapes, and complex contexts, run the FP32
+ * path.  On both tensor-core paths a CTA keeps one pixel per TMEM lane and hands a lane
+ * whose pixel has stopped (Delta < eps) to the next pixel of the cube. */
 cs_status cs_recover_admm(cs_ctx *ctx, const float *Y, float *X, int64_t P, double rho,
                           double lambda, int iters, const cs_opts *opts);
 

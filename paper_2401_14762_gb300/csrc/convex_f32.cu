@@ -568,6 +568,13 @@ __global__ void __launch_bounds__(256, 1) k_measure_tiled(MtParams p) {
     issue(it + ST - 1);
     const float* xb = Xs + (size_t)(it % ST) * kMtP * kMtLdx + (kMtPx * tp) * kMtLdx;
     const int ch = (int)(it % nch);
+    if (p.E && ch == 0) {
+      // the tile's E rows into L2 now, so that the epilogue's loads of them hit L2
+      const int64_t tile = blockIdx.x + (it / nch) * gridDim.x;
+      const int64_t e1 = (tile + 1) * kMtP < p.P ? (tile + 1) * kMtP * M : p.P * M;
+      for (int64_t o = tile * kMtP * M + 32 * (int64_t)tid; o < e1; o += 32 * 256)
+        asm volatile("prefetch.global.L2 [%0];\n" ::"l"(p.E + o));
+    }
     const float* ab = As + tm * lda + ch * kMtK;
 #pragma unroll 1
     for (int k4 = 0; k4 < kMtK / 4; ++k4) {

@@ -414,5 +414,6 @@ def test_fista_maximum_shape(cs):
     ctx = cs.cs_create(128, 256, Phi=pr.Phi)
     for prec in (0, 1):
         Xg, it, _ = gpu_run(cs.cs_recover_fista, ctx, pr.Y, 256, 1e-3, 120, eps=0.0, prec=prec)
+        print(f"FISTA M=128 N=256 prec {prec}: rel-L2 {rel_l2(Xg, Xo):.2e}, tolerance {tol:.2e}")
         assert np.all(it == 120)
         assert rel_l2(Xg, Xo) <= tol
