@@ -596,17 +596,30 @@ __global__ void __launch_bounds__(256, 1) k_measure_tiled(MtParams p) {
     }
     if (ch == nch - 1) {  // the tile is complete: add E, store, restart the sums
       const int64_t tile = blockIdx.x + (it / nch) * gridDim.x;
+      // E through the read-only path, four pixels' rows loaded before any store: plain
+      // loads could alias Y's stores and would each wait for the store before them
+      constexpr int kG = 4;
 #pragma unroll
-      for (int i = 0; i < kMtPx; ++i) {
-        const int64_t pix = tile * kMtP + kMtPx * tp + i;
+      for (int i0 = 0; i0 < kMtPx; i0 += kG) {
+        float ev[kG][RM];
 #pragma unroll
-        for (int r = 0; r < RM; ++r) {
-          const int m = tm + 16 * r;
-          if (pix < p.P && m < M) {
-            const int64_t o = pix * M + m;
-            p.Y[o] = acc[i][r] + (p.E ? p.E[o] : 0.f);
+        for (int i = 0; i < kG; ++i) {
+          const int64_t pix = tile * kMtP + kMtPx * tp + i0 + i;
+#pragma unroll
+          for (int r = 0; r < RM; ++r) {
+            const int m = tm + 16 * r;
+            ev[i][r] = (p.E && pix < p.P && m < M) ? __ldg(p.E + pix * M + m) : 0.f;
           }
-          acc[i][r] = 0.f;
+        }
+#pragma unroll
+        for (int i = 0; i < kG; ++i) {
+          const int64_t pix = tile * kMtP + kMtPx * tp + i0 + i;
+#pragma unroll
+          for (int r = 0; r < RM; ++r) {
+            const int m = tm + 16 * r;
+            if (pix < p.P && m < M) p.Y[pix * M + m] = acc[i0 + i][r] + ev[i][r];
+            acc[i0 + i][r] = 0.f;
+          }
         }
       }
     }
