@@ -17,10 +17,6 @@
  *     With host pointers the library stages the cube through device buffers it owns,
  *     copies on its stream and synchronises before returning.  Both must be of the
  *     same kind.  Optional per-pixel outputs in cs_opts are always device pointers.
- *     Multi-GB host cubes copy at the link's rate when they are page-locked on huge
- *     pages (e.g. cudaHostRegister of an madvise(MADV_HUGEPAGE) mapping): with small
- *     pages the copies of a 6 GB cube slowed to about a third of that rate once other
- *     large buffers had been copied in between.
  *   - Argument errors are reported synchronously, before anything is launched.
  *   - Device-side conditions (non-finite input, a least-squares system that is not
  *     positive definite, an iteration budget that ran out in a bounded wait) are
