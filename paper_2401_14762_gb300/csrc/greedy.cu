@@ -190,15 +190,15 @@ __device__ void load_rhs32(Warp& w) {
 // finish the sum, which leaves atom i's total on lanes 8i..8i+7 after six FP64 additions
 // instead of twenty.  Every total is added in the order a single-value butterfly over
 // lanes 16, 8, 4, 2, 1 apart uses.
-__device__ void ensure_rhs(Warp& w, const int16_t* atoms, int n) {
-  const int M = w.cb->M, lane = w.lane;
-  const double* At = w.cb->At64;
+__device__ __forceinline__ void ensure_rhs_body(const double* At, int M, const double* y64,
+                                                double* bx, uint8_t* bk, const int16_t* atoms,
+                                                int n, int lane) {
   int t = 0;
   for (;;) {
     int j0 = -1, j1 = -1, j2 = -1, j3 = -1;  // warp-uniform (shared-memory broadcasts)
     for (; t < n && j3 < 0; ++t) {
       const int j = atoms[t];
-      if (w.bk[j]) continue;
+      if (bk[j]) continue;
       if (j0 < 0) j0 = j;
       else if (j1 < 0) j1 = j;
       else if (j2 < 0) j2 = j;
@@ -207,7 +207,7 @@ __device__ void ensure_rhs(Warp& w, const int16_t* atoms, int n) {
     if (j0 < 0) return;
     double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
     for (int m = lane; m < M; m += 32) {
-      const double ym = w.y64[m];
+      const double ym = y64[m];
       a0 = fma(__ldg(At + (size_t)j0 * M + m), ym, a0);
       if (j1 >= 0) a1 = fma(__ldg(At + (size_t)j1 * M + m), ym, a1);
       if (j2 >= 0) a2 = fma(__ldg(At + (size_t)j2 * M + m), ym, a2);
@@ -227,12 +227,23 @@ __device__ void ensure_rhs(Warp& w, const int16_t* atoms, int n) {
       const int i = lane >> 3;  // 2 (lane bit 4) + (lane bit 3)
       const int j = i == 0 ? j0 : i == 1 ? j1 : i == 2 ? j2 : j3;
       if (j >= 0) {
-        w.bx[j] = v;
-        w.bk[j] = 1;
+        bx[j] = v;
+        bk[j] = 1;
       }
     }
     __syncwarp();
   }
+}
+
+__device__ __forceinline__ void ensure_rhs(Warp& w, const int16_t* atoms, int n) {
+  ensure_rhs_body(w.cb->At64, w.cb->M, w.y64, w.bx, w.bk, atoms, n, w.lane);
+}
+
+// One out-of-line copy of ensure_rhs for CoSaMP, whose larger least squares leave its
+// hot loop short of instruction-cache room (5% faster there; gOMP and BIHT lose with it).
+__device__ __noinline__ void ensure_rhs_ool(const double* At, int M, const double* y64, double* bx,
+                                           uint8_t* bk, const int16_t* atoms, int n, int lane) {
+  ensure_rhs_body(At, M, y64, bx, bk, atoms, n, lane);
 }
 
 // Appends row n to the factor L of a growing normal-equation system.  g(t) gives the
@@ -702,8 +713,8 @@ __device__ float topk_select_atoms(Warp& w, const float (&val)[kNK], int nvalid,
 // (compared as IEEE bit patterns, which order like the values), or an equal one at a
 // lower position -- and is chosen when fewer than k do.  The order is total, so exactly
 // min(k, cnt) positions are chosen, NaN included.  Output in ascending position order.
-__device__ void topk_select_positions(Warp& w, const double* vals, int cnt, int k, int16_t* out) {
-  const int lane = w.lane;
+__device__ __forceinline__ void topk_positions_body(const double* vals, int cnt, int k,
+                                                    int16_t* out, int lane) {
   const unsigned below = (1u << lane) - 1u;
   const unsigned long long mag = 0x7fffffffffffffffull;
   int pos = 0;
@@ -728,6 +739,16 @@ __device__ void topk_select_positions(Warp& w, const double* vals, int cnt, int 
     pos += __popc(m1);
   }
   __syncwarp();
+}
+
+__device__ __forceinline__ void topk_select_positions(Warp& w, const double* vals, int cnt, int k,
+                                                     int16_t* out) {
+  topk_positions_body(vals, cnt, k, out, w.lane);
+}
+// The same, one out-of-line copy (CoSaMP, as ensure_rhs_ool).
+__device__ __noinline__ void topk_select_positions_ool(const double* vals, int cnt, int k,
+                                                      int16_t* out, int lane) {
+  topk_positions_body(vals, cnt, k, out, lane);
 }
 
 // k rounds of warp argmax over the lane-held values val[kk] (atom lane + 32 kk, only
@@ -1136,7 +1157,9 @@ __global__ void __launch_bounds__(256, 2) k_greedy(GrParams p) {
         const int n = lane + 32 * kk;
         val[kk] = n < N ? w.b32[n] : 0.f;
       }
-#pragma unroll 2
+      // rows of the Gram matrix in flight: BIHT gains from four; gOMP's larger hot loop
+      // loses instruction-cache hits with more than two
+#pragma unroll(ALGO == kBiht ? 4 : 2)
       for (int t = 0; t < nq; ++t) {
         const float xt = w.xqf[t];
         const float* grow = cb.G32 + (size_t)w.q[t] * N;
@@ -1243,7 +1266,10 @@ __global__ void __launch_bounds__(256, 2) k_greedy(GrParams p) {
         __syncwarp();
       }
       // (A^T y)_c as FP32 pairs for the least squares (new atoms only)
-      ensure_rhs(w, w.c, nc);
+      if (ALGO == kCosamp)
+        ensure_rhs_ool(cb.At64, M, w.y64, w.bx, w.bk, w.c, nc, lane);
+      else
+        ensure_rhs(w, w.c, nc);
 
       // ---- step 2: least squares on c ----
       const int nf0 = nf;
@@ -1282,7 +1308,9 @@ __global__ void __launch_bounds__(256, 2) k_greedy(GrParams p) {
       __syncwarp();
       int keep = nc < kappa ? nc : kappa;
       if (nc > kappa) {
-        topk_select_positions(w, w.s, nc, keep, w.sel);  // ascending positions of c
+        // ascending positions of c
+        if (ALGO == kCosamp) topk_select_positions_ool(w.s, nc, keep, w.sel, lane);
+        else topk_select_positions(w, w.s, nc, keep, w.sel);
       } else {
         for (int j = lane; j < nc; j += 32) w.sel[j] = (int16_t)j;
         __syncwarp();
