@@ -239,8 +239,9 @@ __device__ __forceinline__ void ensure_rhs(Warp& w, const int16_t* atoms, int n)
   ensure_rhs_body(w.cb->At64, w.cb->M, w.y64, w.bx, w.bk, atoms, n, w.lane);
 }
 
-// One out-of-line copy of ensure_rhs for CoSaMP, whose larger least squares leave its
-// hot loop short of instruction-cache room (5% faster there; gOMP and BIHT lose with it).
+// One out-of-line copy of ensure_rhs for CoSaMP on supports of more than 64 atoms, whose
+// larger least squares leave the hot loop short of instruction-cache room (5% faster
+// there; gOMP, BIHT and smaller CoSaMP instances lose with it).
 __device__ __noinline__ void ensure_rhs_ool(const double* At, int M, const double* y64, double* bx,
                                            uint8_t* bk, const int16_t* atoms, int n, int lane) {
   ensure_rhs_body(At, M, y64, bx, bk, atoms, n, lane);
@@ -1266,7 +1267,7 @@ __global__ void __launch_bounds__(256, 2) k_greedy(GrParams p) {
         __syncwarp();
       }
       // (A^T y)_c as FP32 pairs for the least squares (new atoms only)
-      if (ALGO == kCosamp)
+      if (ALGO == kCosamp && VR >= 3)
         ensure_rhs_ool(cb.At64, M, w.y64, w.bx, w.bk, w.c, nc, lane);
       else
         ensure_rhs(w, w.c, nc);
@@ -1309,7 +1310,7 @@ __global__ void __launch_bounds__(256, 2) k_greedy(GrParams p) {
       int keep = nc < kappa ? nc : kappa;
       if (nc > kappa) {
         // ascending positions of c
-        if (ALGO == kCosamp) topk_select_positions_ool(w.s, nc, keep, w.sel, lane);
+        if (ALGO == kCosamp && VR >= 3) topk_select_positions_ool(w.s, nc, keep, w.sel, lane);
         else topk_select_positions(w, w.s, nc, keep, w.sel);
       } else {
         for (int j = lane; j < nc; j += 32) w.sel[j] = (int16_t)j;

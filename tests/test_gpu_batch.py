@@ -5,7 +5,7 @@ import numpy as np
 import pytest
 
 import oracle as orc
-from gpu_common import Problem, exact_check, gpu_run, library, torch_cuda
+from gpu_common import Problem, exact_check, gpu_run, library, rel_l2, torch_cuda
 from paper_2401_14762_gb300 import synthetic as sy
 
 pytestmark = pytest.mark.gpu
@@ -222,3 +222,33 @@ def test_batch_replays_in_cuda_graph(cs, algo):
             assert np.array_equal(ig, idd)
             if P:
                 assert np.isfinite(Xd).all() and (idd > 0).all()
+
+
+@pytest.mark.parametrize("prec", [1, 0])
+def test_batch_fista_meets_the_oracle(cs, prec):
+    """The batching workload's FISTA (lambda = 0.1, Delta < 1e-6 or 3,000 iterations) on
+    exactly sparse, noiseless cubes of the three band counts, all in one
+    cs_recover_batch call: every cube within rel-L2 1e-3 of the FP64 oracle run with the
+    same stop rule, on the split-BF16 tensor path and on the FP32 path."""
+    torch = torch_cuda()
+    shapes = [(48, 120, 37), (80, 200, 150), (90, 224, 70)]
+    probs, ctxs, items, outs = [], [], [], []
+    for i, (M, N, P) in enumerate(shapes):
+        S = sy.kappa_per_pixel(P, 4, 32, 60 + i)
+        Phi = sy.gaussian_phi(M, N, 60 + i)
+        A = orc.dictionary(Phi)
+        Y = orc.measure(A, sy.sparse_coeffs(P, N, S, 60 + i), np.zeros((P, M))).astype(np.float32)
+        ctx = cs.cs_create(M, N, Phi=Phi)
+        X = torch.full((P, N), float("nan"), device="cuda")
+        items.append({"ctx": ctx, "Y": torch.from_numpy(Y).cuda(), "X": X})
+        probs.append((A, Y))
+        ctxs.append(ctx)
+        outs.append(X)
+    cs.cs_recover_batch(items, cs.CS_ALGO_FISTA, lam=0.1, iters=3000,
+                        opts=cs.make_opts(eps=1e-6, prec=prec))
+    cs.cs_sync(ctxs[0])
+    for (A, Y), X in zip(probs, outs):
+        Xo, _ = orc.fista(A, Y.astype(np.float64), orc.lipschitz(A), 0.1, 1e-6, 3000)
+        err = rel_l2(X.cpu().numpy(), Xo)
+        print(f"batch FISTA prec {prec}, N = {A.shape[1]}: rel-L2 {err:.2e}")
+        assert err <= 1e-3
