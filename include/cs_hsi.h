@@ -115,8 +115,14 @@ cs_status cs_create(cs_ctx **out, int M, int N, const double *A_host, const doub
  * cs_recover_stream) take Y as P x 2M and X as P x 2N float32, i.e. complex64 arrays of
  * P x M and P x N, and FISTA's and ADMM's soft thresholds act on the moduli |x_k|
  * (x_k scaled by max(|x_k| - t, 0) / |x_k|); L = lambda_max(A^H A).  These run on the
- * FP32 path (prec is ignored).  The greedy calls and cs_sparsify return CS_ERR_ARG on a
- * complex context.  Limits: 1 <= M <= N, M <= 64, N <= 128 (CS_ERR_SHAPE). */
+ * FP32 path (prec is ignored).  cs_recover_gomp, cs_recover_biht and cs_recover_cosamp
+ * (single-cube calls) take the same arrays: kappa and G count complex atoms, each atom
+ * the column pair (2k, 2k + 1) of the real form, selected and pruned by its modulus |x_k|
+ * (FP32 moduli certified against the FP64 modulus, ties to the lower k), so supports and
+ * iteration counts are those of the FP64 complex algorithms.  cs_recover_batch and
+ * cs_recover_stream with a greedy algorithm, cs_autotune and cs_sparsify return
+ * CS_ERR_ARG on a complex context.  Limits: 1 <= M <= N, M <= 64, N <= 128
+ * (CS_ERR_SHAPE). */
 cs_status cs_create_complex(cs_ctx **out, int M, int N, const double *A, double admm_rho,
                             void *cuda_stream);
 

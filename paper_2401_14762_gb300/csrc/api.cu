@@ -485,16 +485,17 @@ static cs_status greedy(cs_ctx* ctx, cs::GreedyAlgo algo, const float* Y, float*
   if (opts) o = *opts;
   if (cs_status s = check_common(ctx, Y, X, P, &o)) return s;
   cs::Ctx& c = ctx->c;
-  if (c.complex_pairs) return arg_error("complex contexts support FISTA and ADMM only");
+  // a complex context counts complex atoms: N / 2 of them on its real form
+  const int Na = c.complex_pairs ? c.N / 2 : c.N;
   int kmax = kappa;
   if (o.kappa_per_pixel) {
     // the caller bounds the per-pixel levels by kappa (used to size the workspace)
-    if (kappa < 0 || kappa > c.N) return arg_error("kappa (upper bound) out of range");
-  } else if (kappa < 0 || kappa > c.N) {
+    if (kappa < 0 || kappa > Na) return arg_error("kappa (upper bound) out of range");
+  } else if (kappa < 0 || kappa > Na) {
     return arg_error("kappa out of range");
   }
-  if (algo == cs::kCosamp && 2 * kmax > c.N) return arg_error("CoSaMP needs 2 kappa <= N");
-  if (algo == cs::kGomp && (G < 0 || G > c.N || (G == 0 && !o.kappa_per_pixel)))
+  if (algo == cs::kCosamp && 2 * kmax > Na) return arg_error("CoSaMP needs 2 kappa <= N");
+  if (algo == cs::kGomp && (G < 0 || G > Na || (G == 0 && !o.kappa_per_pixel)))
     return arg_error("G must be in 1..N (0 only with kappa_per_pixel)");
   if (algo == cs::kBiht && !std::isfinite(o.mu)) return arg_error("mu must be finite");
   if (P == 0) return CS_OK;
@@ -550,7 +551,7 @@ cs_status cs_recover_batch(const cs_batch_item* items, int n_items, cs_algo algo
         (it.kappa_per_pixel && !cs::is_device_ptr(it.kappa_per_pixel)))
       return arg_error("per-pixel arrays must be device memory");
     if (greedy && c.complex_pairs)
-      return arg_error("complex contexts support FISTA and ADMM only");
+      return arg_error("complex contexts run the greedy methods as single-cube calls only");
     if (greedy && it.P > 0) {
       if (kappa < 0 || kappa > c.N) return arg_error("kappa out of range for a cube");
       if (algo == CS_ALGO_COSAMP && 2 * kappa > c.N)
@@ -660,7 +661,7 @@ cs_status cs_recover_stream(cs_ctx* ctx, cs_algo algo, const cs_algo_params* par
   const bool is_greedy = algo >= CS_ALGO_GOMP;
   const int kappa = params->kappa, G = params->G;
   if (is_greedy) {
-    if (c.complex_pairs) return arg_error("complex contexts support FISTA and ADMM only");
+    if (c.complex_pairs) return arg_error("complex contexts run the greedy methods as single-cube calls only");
     if (kappa < 0 || kappa > c.N) return arg_error("kappa out of range");
     if (algo == CS_ALGO_COSAMP && 2 * kappa > c.N) return arg_error("CoSaMP needs 2 kappa <= N");
     if (algo == CS_ALGO_GOMP && (G < 0 || G > c.N || (G == 0 && !o.kappa_per_pixel)))
@@ -797,7 +798,7 @@ cs_status cs_autotune(cs_ctx* ctx, cs_algo algo, const cs_algo_params* params,
   o.kappa_per_pixel = nullptr;
   if (cs_status s = cs::check_opts(o)) return s;
   cs::Ctx& c = ctx->c;
-  if (c.complex_pairs) return arg_error("complex contexts support FISTA and ADMM only");
+  if (c.complex_pairs) return arg_error("complex contexts run the greedy methods as single-cube calls only");
   if (P < 1 || !Y_dev || !cs::is_device_ptr(Y_dev))
     return arg_error("the tuning sample must be P >= 1 pixels in device memory");
   const int kappa = params->kappa, G = algo == CS_ALGO_GOMP ? params->G : 0;
