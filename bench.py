@@ -54,9 +54,9 @@ REL_L2_MIXED = 1e-3
 SM_COUNT, SM_MAX_MHZ = 152, 2070.0
 # Plain-ALU peak derived from unit counts x clock: 128 FP32 FMA lanes per SM.
 FP32_PEAK_TFLOPS = SM_COUNT * 128 * 2 * SM_MAX_MHZ * 1e6 / 1e12
-KERNEL_FILES = {"fista": "fista_tc.cu", "admm": "admm_tc.cu", "measure": "convex_f32.cu",
-                "gomp": "greedy.cu", "biht": "greedy.cu", "cosamp": "greedy.cu",
-                "sparsify": "sparsify.cu"}
+_GREEDY = ("greedy_kernel.cuh", "greedy.cu")
+KERNEL_FILES = {"fista": ("fista_tc.cu",), "admm": ("admm_tc.cu",), "measure": ("convex_f32.cu",),
+                "gomp": _GREEDY, "biht": _GREEDY, "cosamp": _GREEDY, "sparsify": ("sparsify.cu",)}
 
 
 def config(extra=None):
@@ -228,8 +228,11 @@ class ClockSampler:
 
 # ----------------------------------------------------------------------------- helpers
 def kernel_hash(name):
-    src = os.path.join(ROOT, "paper_2401_14762_gb300", "csrc", KERNEL_FILES[name])
-    return hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    """sha256 prefix of the kernel's source files (concatenated in order)."""
+    h = hashlib.sha256()
+    for f in KERNEL_FILES[name]:
+        h.update(open(os.path.join(ROOT, "paper_2401_14762_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
 
 
 def measured_traffic(name, workload):
