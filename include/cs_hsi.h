@@ -119,10 +119,10 @@ cs_status cs_create(cs_ctx **out, int M, int N, const double *A_host, const doub
  * (single-cube calls) take the same arrays: kappa and G count complex atoms, each atom
  * the column pair (2k, 2k + 1) of the real form, selected and pruned by its modulus |x_k|
  * (FP32 moduli certified against the FP64 modulus, ties to the lower k), so supports and
- * iteration counts are those of the FP64 complex algorithms.  cs_recover_batch and
- * cs_recover_stream with a greedy algorithm, cs_autotune and cs_sparsify return
- * CS_ERR_ARG on a complex context.  Limits: 1 <= M <= N, M <= 64, N <= 128
- * (CS_ERR_SHAPE). */
+ * iteration counts are those of the FP64 complex algorithms; they also run in
+ * cs_recover_stream and in cs_recover_batch (a greedy batch is all complex or all real).
+ * cs_autotune and cs_sparsify return CS_ERR_ARG on a complex context.  Limits:
+ * 1 <= M <= N, M <= 64, N <= 128 (CS_ERR_SHAPE). */
 cs_status cs_create_complex(cs_ctx **out, int M, int N, const double *A, double admm_rho,
                             void *cuda_stream);
 

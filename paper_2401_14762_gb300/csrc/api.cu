@@ -550,13 +550,14 @@ cs_status cs_recover_batch(const cs_batch_item* items, int n_items, cs_algo algo
         (it.converged_out && !cs::is_device_ptr(it.converged_out)) ||
         (it.kappa_per_pixel && !cs::is_device_ptr(it.kappa_per_pixel)))
       return arg_error("per-pixel arrays must be device memory");
-    if (greedy && c.complex_pairs)
-      return arg_error("complex contexts run the greedy methods as single-cube calls only");
+    if (greedy && c.complex_pairs != items[0].ctx->c.complex_pairs)
+      return arg_error("a greedy batch cannot mix complex and real contexts");
     if (greedy && it.P > 0) {
-      if (kappa < 0 || kappa > c.N) return arg_error("kappa out of range for a cube");
-      if (algo == CS_ALGO_COSAMP && 2 * kappa > c.N)
+      const int Na = c.complex_pairs ? c.N / 2 : c.N;  // complex contexts count complex atoms
+      if (kappa < 0 || kappa > Na) return arg_error("kappa out of range for a cube");
+      if (algo == CS_ALGO_COSAMP && 2 * kappa > Na)
         return arg_error("CoSaMP needs 2 kappa <= N for every cube");
-      if (algo == CS_ALGO_GOMP && (G < 0 || G > c.N || (G == 0 && !it.kappa_per_pixel)))
+      if (algo == CS_ALGO_GOMP && (G < 0 || G > Na || (G == 0 && !it.kappa_per_pixel)))
         return arg_error("G must be in 1..N (0 only with kappa_per_pixel)");
     }
   }
@@ -661,10 +662,10 @@ cs_status cs_recover_stream(cs_ctx* ctx, cs_algo algo, const cs_algo_params* par
   const bool is_greedy = algo >= CS_ALGO_GOMP;
   const int kappa = params->kappa, G = params->G;
   if (is_greedy) {
-    if (c.complex_pairs) return arg_error("complex contexts run the greedy methods as single-cube calls only");
-    if (kappa < 0 || kappa > c.N) return arg_error("kappa out of range");
-    if (algo == CS_ALGO_COSAMP && 2 * kappa > c.N) return arg_error("CoSaMP needs 2 kappa <= N");
-    if (algo == CS_ALGO_GOMP && (G < 0 || G > c.N || (G == 0 && !o.kappa_per_pixel)))
+    const int Na = c.complex_pairs ? c.N / 2 : c.N;  // complex contexts count complex atoms
+    if (kappa < 0 || kappa > Na) return arg_error("kappa out of range");
+    if (algo == CS_ALGO_COSAMP && 2 * kappa > Na) return arg_error("CoSaMP needs 2 kappa <= N");
+    if (algo == CS_ALGO_GOMP && (G < 0 || G > Na || (G == 0 && !o.kappa_per_pixel)))
       return arg_error("G must be in 1..N (0 only with kappa_per_pixel)");
     if (algo == CS_ALGO_BIHT && !std::isfinite(o.mu)) return arg_error("mu must be finite");
   } else {

@@ -350,7 +350,9 @@ cudaError_t launch_greedy_batch(Ctx& c0, GreedyAlgo algo, const GreedyCube* cube
     if (g.ctx->N > Nmax) Nmax = g.ctx->N;
   }
   if (total == 0) return cudaSuccess;
-  return run_greedy(c0, algo, a, host.data(), (int)host.size(), Mmax, Nmax, total);
+  // the caller checked that the cubes are all complex (column pairs) or all real
+  return run_greedy(c0, algo, a, host.data(), (int)host.size(), Mmax, Nmax, total,
+                    c0.complex_pairs);
 }
 
 }  // namespace cs

@@ -173,23 +173,54 @@ def test_complex_greedy_matches_oracle(cs, algo, noise):
     assert err <= 1e-5
 
 
-def test_complex_greedy_refuses_batches_and_streams(cs):
-    """Complex contexts run the greedy methods as single-cube calls; batches and streams
-    refuse them with an argument error, and kappa counts complex atoms."""
+def test_complex_greedy_in_streams_and_batches(cs):
+    """The complex greedy methods in cs_recover_stream (ragged chunks, pinned host memory)
+    and in cs_recover_batch (two complex cubes of different shapes) give the single
+    calls' X and iteration counts bit for bit; a batch mixing complex and real contexts,
+    and kappa above the complex N, are refused."""
     torch = torch_cuda()
-    M, N = 24, 64
-    A, Y = _problem(M, N, 8, 13)
-    ctx = cs.cs_create_complex(M, N, A)
-    Yh = np.ascontiguousarray(Y).view(np.float32)
-    Xh = np.zeros((8, 2 * N), dtype=np.float32)
+    shapes = [(24, 64, 37), (30, 100, 50)]
+    probs = [_problem(M, N, P, 20 + i, S=4) for i, (M, N, P) in enumerate(shapes)]
+    ctxs = [cs.cs_create_complex(M, N, A) for (M, N, _), (A, _) in zip(shapes, probs)]
+    singles = {}
+    for algo, code in (("gomp", cs.CS_ALGO_GOMP), ("biht", cs.CS_ALGO_BIHT),
+                       ("cosamp", cs.CS_ALGO_COSAMP)):
+        for i, ((M, N, P), (A, Y), ctx) in enumerate(zip(shapes, probs, ctxs)):
+            singles[algo, i] = _greedy(cs, ctx, algo, Y, N, 6)
+        # stream, first cube
+        (M, N, P), (A, Y), ctx = shapes[0], probs[0], ctxs[0]
+        Yh = torch.from_numpy(np.ascontiguousarray(Y).view(np.float32)).pin_memory()
+        Xh = torch.full((P, 2 * N), float("nan")).pin_memory()
+        it = torch.full((P,), -1, device="cuda", dtype=torch.int32)
+        cs.cs_recover_stream(ctx, code, Yh, Xh, 16, kappa=6, G=2 if algo == "gomp" else 0,
+                             opts=cs.make_opts(mu=1.0, iters_out=it))
+        Xs = Xh.numpy().view(np.complex64).astype(np.complex128)
+        assert np.array_equal(Xs, singles[algo, 0][0]) and np.array_equal(it.cpu().numpy(),
+                                                                           singles[algo, 0][1])
+        # batch of both cubes
+        items, outs = [], []
+        for (M, N, P), (A, Y), ctx in zip(shapes, probs, ctxs):
+            Yd = torch.from_numpy(np.ascontiguousarray(Y).view(np.float32)).cuda()
+            Xd = torch.full((P, 2 * N), float("nan"), device="cuda")
+            itd = torch.full((P,), -1, device="cuda", dtype=torch.int32)
+            items.append({"ctx": ctx, "Y": Yd, "X": Xd, "iters_out": itd})
+            outs.append((Xd, itd))
+        cs.cs_recover_batch(items, code, kappa=6, G=2 if algo == "gomp" else 0,
+                            opts=cs.make_opts(mu=1.0))
+        cs.cs_sync(ctxs[0])
+        for i, (Xd, itd) in enumerate(outs):
+            Xb = Xd.cpu().numpy().view(np.complex64).astype(np.complex128)
+            assert np.array_equal(Xb, singles[algo, i][0])
+            assert np.array_equal(itd.cpu().numpy(), singles[algo, i][1])
+    # a real context beside a complex one, and kappa above the complex N
+    real = cs.cs_create(48, 128, Phi=np.random.default_rng(0).standard_normal((48, 128)) / 7)
+    Yd = torch.zeros((4, 48), device="cuda")
+    Yc = torch.zeros((4, 48), device="cuda")
     with pytest.raises(cs.CsError) as e:
-        cs.cs_recover_stream(ctx, cs.CS_ALGO_GOMP, Yh, Xh, 4, kappa=4, G=2)
-    assert e.value.status == cs.CS_ERR_ARG
-    Yd = torch.from_numpy(Yh).cuda()
-    with pytest.raises(cs.CsError) as e:
-        cs.cs_recover_batch([{"ctx": ctx, "Y": Yd, "X": torch.zeros((8, 2 * N), device="cuda")}],
+        cs.cs_recover_batch([{"ctx": ctxs[0], "Y": Yc, "X": torch.zeros((4, 128), device="cuda")},
+                             {"ctx": real, "Y": Yd, "X": torch.zeros((4, 128), device="cuda")}],
                             cs.CS_ALGO_COSAMP, kappa=4)
     assert e.value.status == cs.CS_ERR_ARG
     with pytest.raises(cs.CsError) as e:  # kappa counts complex atoms: at most N
-        cs.cs_recover_gomp(ctx, Yd, torch.zeros((8, 2 * N), device="cuda"), N + 1, 2)
+        cs.cs_recover_gomp(ctxs[0], Yc, torch.zeros((4, 128), device="cuda"), 65, 2)
     assert e.value.status == cs.CS_ERR_ARG
