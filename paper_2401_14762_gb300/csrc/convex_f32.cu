@@ -16,9 +16,14 @@
 //   (A^T A + rho I)^{-1} v = (v - A^T W A v) / rho,  W = (A A^T + rho I)^{-1},
 // which with d = z - w and h = W (y - A d) gives x = d + A^T h and A x = y - rho h, so
 // r^i = rho h^i: 4MN + 2M^2 flops per iteration, Delta again for free.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
+#include <mutex>
+
 #include "cs_internal.cuh"
+#include "tc_ptx.cuh"
 
 namespace cs {
 namespace {
@@ -483,90 +488,90 @@ __global__ void __launch_bounds__(kThreads, 1) k_measure_f32(CvParams p) {
 // Eq. 1 measurement for N a multiple of 4: Y = X A^T (+ E) as a register-tiled SIMT
 // product.  Persistent CTAs of 256 threads walk tiles of 256 pixels; A (rows padded to
 // 16 RM with zeros, columns to a multiple of 32) stays in shared memory, and the tile's X
-// arrives in chunks of 32 columns through a cp.async ring (3 stages, 2 when A is large),
-// so the next chunks stream from HBM while the current one is multiplied.  Thread
-// (tp, tm) of the 16 x 16 grid owns pixels 16 tp .. 16 tp + 15 and rows tm + 16 r
-// (r < RM): per float4 step of k it reads 16 float4 of X and RM of A for 64 RM FMAs, so
-// shared memory (one 8-lane wavefront per cycle) keeps up with the FMA pipes.  Each
-// output is summed in the order k = 0, 1, ..., N-1.
+// arrives in boxes of 256 pixels x 32 columns that one thread requests from the tensor
+// memory accelerator (TMA: cp.async.bulk.tensor with an mbarrier per stage of a 3-stage
+// ring), so the next boxes stream from HBM while the current one is multiplied; rows past
+// P and columns past N arrive as zeros.  Thread (tp, tm) of the 16 x 16 grid owns pixels
+// 16 tp .. 16 tp + 15 and rows tm + 16 r (r < RM): per float4 step of k it reads 16
+// float4 of X and RM of A for 64 RM FMAs, so shared memory (one 8-lane wavefront per
+// cycle) keeps up with the FMA pipes.  Each output is summed in the order k = 0, 1, ...
 // ---------------------------------------------------------------------------------
 struct MtParams {
   int M, N, lda;   // lda: row stride of A in shared memory
   const float* A;  // M x N global
-  const float* X;  // P x N
+  const float* X;  // P x N (read through the tensor map)
   const float* E;  // P x M or null
   float* Y;        // P x M
   int64_t P;
+  int* status;     // the context's status word (a TMA box that never arrived)
 };
 
-constexpr int kMtP = 256;            // pixels per tile
+constexpr int kMtP = 256;            // pixels per tile (TMA box rows)
 constexpr int kMtPx = kMtP / 16;     // pixels per thread
-constexpr int kMtK = 32;             // columns per chunk
-constexpr int kMtLdx = kMtK + 4;     // row stride of a staged X chunk (16-byte rows)
-// stages of the X ring beside A (16 RM rows of lda floats)
-__host__ __device__ constexpr int mt_stages(int rm, int lda) {
-  return 4 * (16 * rm * lda + 3 * kMtP * kMtLdx) <= 227 * 1024 ? 3 : 2;
+constexpr int kMtK = 32;             // columns per chunk (TMA box columns: 128 bytes)
+constexpr int kMtStages = 3;
+constexpr uint64_t kMtWaitNs = 100ull * 1000 * 1000;  // 100 ms for one box
+// bytes of A in shared memory, rounded up so that the X ring starts 1024-byte aligned
+__host__ __device__ constexpr int mt_abytes(int rm, int lda) {
+  return (4 * 16 * rm * lda + 1023) / 1024 * 1024;
 }
 
-__device__ __forceinline__ void cp_async16(float* dst, const float* src, bool valid) {
-  const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(dst));
-  const int n = valid ? 16 : 0;  // 0: the 16 bytes are zero-filled, nothing is read
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(src), "r"(n)
-               : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() {
-  asm volatile("cp.async.commit_group;\n" ::: "memory");
-}
-template <int N>
-__device__ __forceinline__ void cp_async_wait() {
-  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
-}
-
-template <int RM, int ST>
-__global__ void __launch_bounds__(256, 1) k_measure_tiled(MtParams p) {
-  extern __shared__ __align__(16) float sm[];
+template <int RM>
+__global__ void __launch_bounds__(256, 1)
+    k_measure_tiled(MtParams p, const __grid_constant__ CUtensorMap tmap) {
+  extern __shared__ __align__(1024) unsigned char msm[];
+  __shared__ __align__(8) uint64_t mbx[kMtStages];
   const int M = p.M, N = p.N, lda = p.lda;
-  float* As = sm;                 // 16 RM x lda
-  float* Xs = As + 16 * RM * lda; // kMtStages x kMtP x kMtLdx
+  float* As = reinterpret_cast<float*>(msm);                       // 16 RM x lda
+  float* Xs = reinterpret_cast<float*>(msm + mt_abytes(RM, lda));  // stages x kMtP x kMtK
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int tm = lane & 15, tp = (lane >> 4) + 2 * warp;
+  if (tid == 0)
+    for (int s = 0; s < kMtStages; ++s) tc::mbar_init(&mbx[s], 1);
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   for (int i = tid; i < 16 * RM * lda; i += 256) {
     const int r = i / lda, c = i - r * lda;
     As[i] = (r < M && c < N) ? p.A[(size_t)r * N + c] : 0.f;
   }
+  __syncthreads();
   const int nch = (N + kMtK - 1) / kMtK;
   const int64_t ntiles = (p.P + kMtP - 1) / kMtP;
   const int64_t my_tiles = ntiles > blockIdx.x ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
-  const int64_t items = my_tiles * nch;  // (tile, chunk) pairs of this CTA, in order
-  // thread tid copies float4 j of the chunk: pixel (tid + 256 j) / 8, column group % 8
+  const int64_t items = my_tiles * nch;  // (tile, chunk) boxes of this CTA, in order
+  // box `it` into stage it % kMtStages, by thread 0; the readers of the stage's previous
+  // box have passed a barrier since
   auto issue = [&](int64_t it) {
-    if (it < items) {
-      const int64_t tile = blockIdx.x + (it / nch) * gridDim.x;
-      const int ch = (int)(it % nch);
-      float* dst = Xs + (size_t)(it % ST) * kMtP * kMtLdx;
-#pragma unroll
-      for (int j = 0; j < kMtP * kMtK / 4 / 256; ++j) {
-        const int idx = tid + 256 * j, px = idx >> 3, k4 = idx & 7;
-        const int64_t pix = tile * kMtP + px;
-        const int col = ch * kMtK + 4 * k4;
-        const bool ok = pix < p.P && col < N;
-        cp_async16(dst + px * kMtLdx + 4 * k4, ok ? p.X + pix * N + col : p.X, ok);
-      }
-    }
-    cp_async_commit();  // one group per item, empty past the end, so the counts stay aligned
+    if (tid != 0 || it >= items) return;
+    const int64_t tile = blockIdx.x + (it / nch) * gridDim.x;
+    const int s = (int)(it % kMtStages);
+    const uint32_t dst = tc::smem_u32(Xs + (size_t)s * kMtP * kMtK);
+    const uint32_t mb = tc::smem_u32(&mbx[s]);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mb),
+                 "r"(kMtP * kMtK * 4)
+                 : "memory");
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes "
+        "[%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(&tmap)), "r"((int)(it % nch) * kMtK),
+        "r"((int)(tile * kMtP)), "r"(mb)
+        : "memory");
   };
 #pragma unroll
-  for (int s = 0; s < ST - 1; ++s) issue(s);
+  for (int s = 0; s < kMtStages - 1; ++s) issue(s);
   float acc[kMtPx][RM];
 #pragma unroll
   for (int i = 0; i < kMtPx; ++i)
 #pragma unroll
     for (int r = 0; r < RM; ++r) acc[i][r] = 0.f;
-  for (int64_t it = 0; it < items; ++it) {
-    cp_async_wait<ST - 2>();
-    __syncthreads();  // chunk it is in place; every thread is done with chunk it - 1
-    issue(it + ST - 1);
-    const float* xb = Xs + (size_t)(it % ST) * kMtP * kMtLdx + (kMtPx * tp) * kMtLdx;
+  int64_t it = 0;
+  for (; it < items; ++it) {
+    const bool got = tc::mbar_wait(&mbx[it % kMtStages], (uint32_t)((it / kMtStages) & 1),
+                                   kMtWaitNs);
+    // box it is in place (or never came); every thread is done with box it - 1
+    if (__syncthreads_or(!got)) break;
+    issue(it + kMtStages - 1);
+    const float* xb = Xs + (size_t)(it % kMtStages) * kMtP * kMtK + (kMtPx * tp) * kMtK;
     const int ch = (int)(it % nch);
     if (p.E && ch == 0) {
       // the tile's E rows into L2 now, so that the epilogue's loads of them hit L2
@@ -581,7 +586,7 @@ __global__ void __launch_bounds__(256, 1) k_measure_tiled(MtParams p) {
       float4 xv[kMtPx];
 #pragma unroll
       for (int i = 0; i < kMtPx; ++i)
-        xv[i] = *reinterpret_cast<const float4*>(xb + i * kMtLdx + 4 * k4);
+        xv[i] = *reinterpret_cast<const float4*>(xb + i * kMtK + 4 * k4);
 #pragma unroll
       for (int r = 0; r < RM; ++r) {
         const float4 a = *reinterpret_cast<const float4*>(ab + 16 * r * lda + 4 * k4);
@@ -624,28 +629,57 @@ __global__ void __launch_bounds__(256, 1) k_measure_tiled(MtParams p) {
       }
     }
   }
-  cp_async_wait<0>();
+  if (it < items && tid == 0) {
+    // a box never arrived: report it, and give the boxes still in flight (it .. it +
+    // stages - 2) one more bounded wait before the CTA's shared memory is released
+    atomicOr(p.status, kStTimeout);
+    for (int64_t j = it; j < items && j < it + kMtStages - 1; ++j)
+      tc::mbar_wait(&mbx[j % kMtStages], (uint32_t)((j / kMtStages) & 1), kMtWaitNs);
+  }
 }
 
-template <int RM, int ST>
-static cudaError_t measure_tiled_st(const Ctx& c, MtParams p, size_t smem) {
-  cudaError_t e = cudaFuncSetAttribute(k_measure_tiled<RM, ST>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  const int64_t ntiles = (p.P + kMtP - 1) / kMtP;
-  const int64_t grid = ntiles < c.num_sms ? ntiles : c.num_sms;
-  k_measure_tiled<RM, ST><<<(unsigned)grid, 256, smem, c.stream>>>(p);
-  return cudaGetLastError();
+// cuTensorMapEncodeTiled from the driver, looked up once through the runtime.
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+  });
+  return fn;
 }
 
 template <int RM>
 static cudaError_t measure_tiled(const Ctx& c, MtParams p) {
   const int kpad = (c.N + kMtK - 1) / kMtK * kMtK;
   p.lda = kpad + 4;  // 16-byte rows; 8 consecutive rows fall on distinct 4-bank groups
-  const int st = mt_stages(RM, p.lda);
-  const size_t smem = sizeof(float) * ((size_t)16 * RM * p.lda + (size_t)st * kMtP * kMtLdx);
+  const size_t smem = (size_t)mt_abytes(RM, p.lda) + (size_t)kMtStages * kMtP * kMtK * 4;
   if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
-  return st == 3 ? measure_tiled_st<RM, 3>(c, p, smem) : measure_tiled_st<RM, 2>(c, p, smem);
+  // X as a 2-D tensor of N columns (16-byte row stride: N is a multiple of 4) and P rows,
+  // read in boxes of kMtK x kMtP: every box starts at a column that is a multiple of 32
+  // (128 bytes) and a row that is a multiple of 256
+  PFN_cuTensorMapEncodeTiled_v12000 encode = tensor_map_encoder();
+  if (!encode) return cudaErrorNotSupported;
+  CUtensorMap tmap;
+  const cuuint64_t dims[2] = {(cuuint64_t)c.N, (cuuint64_t)p.P};
+  const cuuint64_t strides[1] = {(cuuint64_t)c.N * sizeof(float)};
+  const cuuint32_t box[2] = {(cuuint32_t)kMtK, (cuuint32_t)kMtP};
+  const cuuint32_t estr[2] = {1, 1};
+  if (encode(&tmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(p.X), dims, strides,
+             box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    return cudaErrorInvalidValue;
+  cudaError_t e = cudaFuncSetAttribute(k_measure_tiled<RM>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const int64_t ntiles = (p.P + kMtP - 1) / kMtP;
+  const int64_t grid = ntiles < c.num_sms ? ntiles : c.num_sms;
+  k_measure_tiled<RM><<<(unsigned)grid, 256, smem, c.stream>>>(p, tmap);
+  return cudaGetLastError();
 }
 
 // Momentum weights of Algorithm 1 steps 3-4: t_0 = 1, t_i = (1 + sqrt(1 + 4 t_{i-1}^2)) / 2,
@@ -812,8 +846,10 @@ cudaError_t launch_measure(const Ctx& c, const float* X, float* Y, const float* 
   p.E = E;
   p.P = P;
   if (P == 0) return cudaSuccess;
-  if (c.N % 4 == 0 && c.M <= 128 && (reinterpret_cast<uintptr_t>(X) & 15) == 0) {
-    MtParams q{c.M, c.N, 0, c.A32, X, E, Y, P};
+  // the tiled kernel's tensor map addresses rows with 32-bit coordinates
+  if (c.N % 4 == 0 && c.M <= 128 && (reinterpret_cast<uintptr_t>(X) & 15) == 0 &&
+      P < ((int64_t)1 << 31) - kMtP) {
+    MtParams q{c.M, c.N, 0, c.A32, X, E, Y, P, c.status};
     switch ((c.M + 15) / 16) {
       case 1: return measure_tiled<1>(c, q);
       case 2: return measure_tiled<2>(c, q);
