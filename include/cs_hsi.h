@@ -139,7 +139,9 @@ cs_status cs_get_dictionary(const cs_ctx *ctx, double *A_host);
  * additive noise or NULL (the same kind of memory as X and Y).  FP32 arithmetic.  A
  * cube in host memory is measured in chunks of 262,144 pixels whose copies in and out
  * overlap the kernel (pinned memory lets them); the results equal a device-memory
- * call's bit for bit. */
+ * call's bit for bit.  With N a multiple of 4 and a 16-byte-aligned device X, X is read
+ * through a tensor map in 256-pixel x 32-column boxes; a box that has not arrived after
+ * 100 ms stops the kernel and latches CS_ERR_TIMEOUT, returned by the next cs_sync. */
 cs_status cs_measure(cs_ctx *ctx, const float *X, float *Y, const float *E, int64_t P);
 
 /* FISTA, Algorithm 1: x^0 = z^0 = 0, t^0 = 1; per iteration
