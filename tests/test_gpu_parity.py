@@ -77,6 +77,32 @@ def test_measure(cs, M, N):
     assert (np.abs(Yd.cpu().numpy() - ref) / scale).max() < 1e-6
 
 
+@pytest.mark.parametrize("M,N,P,offset", [(2, 4, 1, 0), (3, 8, 37, 0), (16, 32, 255, 0),
+                                          (20, 60, 257, 0), (5, 28, 600, 0), (48, 120, 1000, 1),
+                                          (102, 256, 513, 2)])
+def test_measure_edges(cs, M, N, P, offset):
+    """The tiled kernel's tensor-map boxes (256 pixels x 32 columns) wider than X (N < 32)
+    or taller (P < 256), ending inside a column chunk or a tile, and X starting off a
+    16-byte boundary (offset floats into its buffer), which takes the general kernel."""
+    torch = pytest.importorskip("torch")
+    Phi = sy.gaussian_phi(M, N, 4)
+    A = orc.dictionary(Phi)
+    X = sy.powerlaw_coeffs(P, N, 4, permute=True).astype(np.float32)
+    E = sy.noise(P, M, 1e-3, 4).astype(np.float32)
+    ctx = cs.cs_create(M, N, Phi=Phi)
+    buf = torch.zeros(P * N + 4, device="cuda")
+    Xd = buf[offset:offset + P * N].view(P, N)
+    Xd.copy_(torch.from_numpy(X))
+    assert (Xd.data_ptr() % 16 == 0) == (offset == 0)
+    Yd = torch.full((P, M), float("nan"), device="cuda")
+    Ed = torch.from_numpy(E).cuda()
+    cs.cs_measure(ctx, Xd, Yd, Ed)
+    cs.cs_sync(ctx)
+    ref = orc.measure(A, X.astype(np.float64), E.astype(np.float64))
+    scale = np.linalg.norm(ref, axis=1, keepdims=True)
+    assert (np.abs(Yd.cpu().numpy() - ref) / scale).max() < 1e-6
+
+
 # --------------------------------------------------------------------------- FISTA
 def _fista_fixed(cs, pr, lam, iters):
     """A fixed, unconverged iteration count: the oracle's own output is ill-conditioned
