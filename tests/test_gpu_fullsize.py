@@ -1,7 +1,7 @@
 """The bench's workloads at full size, in the launch configuration bench.py times: the
 2048 x 2048 x 256 cube (M = 102) of the headline and the 1024 x 1024 x 224 cube (M = 90)
-beside it, measured on the GPU and every pixel recovered by all five algorithms with the
-bench's options (FISTA and ADMM on the mixed path where a tensor-core tile exists).
+beside it, measured on the GPU (the sampled measurements checked against the oracle's)
+and every pixel recovered by all five algorithms with the bench's options (FISTA and ADMM on the mixed path where a tensor-core tile exists).
 384 pixels spread over the cube, plus its first and last, are recovered by the FP64
 oracle from the same FP32 measurements: the greedy pixels must follow the oracle's
 trajectories exactly, FISTA and ADMM stay within the metric's rel-L2 of 1e-3."""
@@ -70,6 +70,9 @@ def test_full_cube_sampled_against_oracle(cs, workload):
     Ys = Y[sel].cpu().numpy()  # the FP32 measurements both sides recover from
     A = orc.dictionary(Phi)
     L = orc.lipschitz(A)
+    # the measurement itself (the TMA-fed tiled kernel over the whole cube) at the samples
+    Yo = orc.measure(A, Xt[sel].cpu().double().numpy(), E[sel].cpu().double().numpy())
+    assert (np.abs(Ys - Yo) / np.linalg.norm(Yo, axis=1, keepdims=True)).max() < 1e-6
     g = {a: out[a][sel].cpu().numpy() for a in out}
     gi = {a: its[a][sel].cpu().numpy() for a in its}
     ef = rel_l2(g["fista"], orc.fista(A, Ys, L, bench.LAM, bench.EPS, bench.ITERS)[0])
